@@ -1,0 +1,370 @@
+"""Pins of the CPU oracle against things other than itself: values the paper
+prints, closed forms, integral representations evaluated by quadrature,
+finite differences of the defining potentials, exact invariants of the
+discrete method and the classical Lorenz-Mie solution.  CPU only."""
+import math
+import os
+
+import mpmath
+import numpy as np
+import pytest
+from scipy.special import hankel1, kv
+
+from oracle import field, green, losses, physics, run
+from oracle.constants import C_LIGHT, E_CHARGE, EPS0, HBAR, MU0, NM, Q_ELECTRON
+from oracle.icosphere import icosphere
+from oracle.mie import mie_cross_sections
+from paper_2208_01348_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _host(eps_h, ekin, e_eV):
+    v = physics.electron_speed(ekin)
+    m_h = physics.host_index(eps_h)
+    beta, gamma = physics.beta_gamma_h(v, m_h)
+    return v, m_h, beta, gamma, float(physics.omega_of(e_eV))
+
+
+HOSTS = [  # (eps_h, ekin keV, energy eV): vacuum, glass, dense absorbing (Cherenkov), absorbing sub-threshold
+    (1.0, 100.0, 2.4), (2.1025, 120.0, 3.1), (4.0 + 0.05j, 200.0, 2.7), (2.0 + 0.6j, 100.0, 1.7),
+    (4.0 + 1.0j, 200.0, 3.3), (3.2, 100.0, 2.8),
+]
+
+
+# ---------------------------------------------------------------- kinematics
+def test_golden_beta_h_printed_in_paper():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "paper_beta_h.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for ek, eps, voc, beta_p, dec, _cite in rows:
+        v = physics.electron_speed(float(ek))
+        beta, _ = physics.beta_gamma_h(v, physics.host_index(float(eps)))
+        if voc != "nan":
+            assert round(v / C_LIGHT, int(dec)) == pytest.approx(float(voc))
+        assert round(beta.real, int(dec)) == pytest.approx(float(beta_p))
+        assert beta.imag == 0.0
+
+
+def test_eq47_kinetic_energy_map_scales_speed_by_m_h():
+    for ek in (60.0, 100.0, 200.0):
+        for eps_h in (1.21, 1.69, 2.1025):
+            v = physics.electron_speed(ek)
+            if math.sqrt(eps_h) * v >= C_LIGHT:
+                continue
+            v2 = physics.electron_speed(physics.scaled_kinetic_energy(ek, eps_h))
+            assert v2 == pytest.approx(math.sqrt(eps_h) * v, rel=1e-12)
+
+
+def test_gamma_h_first_quadrant_and_cherenkov_limit():
+    v = physics.electron_speed(200.0)
+    for mag in (0.5, 1.0, 2.0, 4.0, 9.0):
+        for arg in np.linspace(0.0, 0.95 * np.pi, 9):
+            eps = mag * np.exp(1j * arg)
+            _, g = physics.beta_gamma_h(v, physics.host_index(eps))
+            assert g.real >= -1e-15 and g.imag >= -1e-15
+    # real beta_h > 1 is the limit Im eps_h -> 0+ (Sec. 2.2)
+    _, g0 = physics.beta_gamma_h(v, physics.host_index(4.0))
+    _, g1 = physics.beta_gamma_h(v, physics.host_index(4.0 + 1e-10j))
+    assert abs(g0 - g1) < 1e-8 * abs(g0)
+    assert g0.real == 0.0 and g0.imag > 0
+    with pytest.raises(ValueError):
+        physics.beta_gamma_h(C_LIGHT / 1.5, 1.5)
+
+
+# ---------------------------------------------------------------- K0 / K1
+def test_scipy_kv_matches_mpmath_in_fourth_quadrant():
+    mpmath.mp.dps = 30
+    for mag in np.geomspace(1e-3, 20.0, 15):
+        for arg in np.linspace(-np.pi / 2, 0.0, 9):
+            z = mag * np.exp(1j * arg)
+            for nu in (0, 1):
+                ref = complex(mpmath.besselk(nu, mpmath.mpc(z.real, z.imag)))
+                assert abs(kv(nu, z) - ref) <= 1e-13 * abs(ref), (nu, z)
+
+
+def test_kv_on_imaginary_axis_is_hankel():
+    # K0(-ix) = (i pi/2) H0(1)(x), K1(-ix) = -(pi/2) H1(1)(x)  (DLMF 10.27.8)
+    for x in (0.01, 0.3, 1.0, 3.1, 12.0):
+        assert abs(kv(0, -1j * x) - 0.5j * np.pi * hankel1(0, x)) < 1e-13 * abs(hankel1(0, x))
+        assert abs(kv(1, -1j * x) + 0.5 * np.pi * hankel1(1, x)) < 1e-13 * abs(hankel1(1, x))
+
+
+@pytest.mark.parametrize("eps_h,ekin,e_eV,b_nm", [
+    (2.0 + 0.6j, 100.0, 1.7, 12.0),      # absorbing, beta_h < 1
+    (4.0 + 1.0j, 200.0, 3.3, 25.0),      # absorbing, Re beta_h > 1 (Cherenkov)
+    (9.0 + 2.0j, 300.0, 2.0, 5.0),
+])
+def test_I1_equals_quadrature_of_eq_S8(eps_h, ekin, e_eV, b_nm):
+    """Eq. S8: I_S(b) = int du exp(i (w b/v)(beta_h cosh u - sinh u)) = 2 K0(k_t b),
+    k_t = w/(gamma_h v).  With Im beta_h > 0 the integrand decays
+    double-exponentially and the trapezoid rule converges fast."""
+    v, m_h, beta, gamma, w = _host(eps_h, ekin, e_eV)
+    b = b_nm * NM
+    a = w * b / v
+    umax = math.acosh(60.0 / (a * beta.imag)) + 0.5
+    u = np.linspace(-umax, umax, 400001)
+    f = np.exp(1j * a * (beta * np.cosh(u) - np.sinh(u)))
+    quad = np.trapezoid(f, u)
+    ref = 2.0 * kv(0, w * b / (gamma * v))
+    assert abs(quad - ref) < 1e-9 * abs(ref)
+
+
+# ---------------------------------------------------------------- fields
+def _fd_grad_xy(f, r, h):
+    out = []
+    for ax in (0, 1):
+        e = np.zeros(3)
+        e[ax] = h
+        out.append((-f(r + 2 * e) + 8 * f(r + e) - 8 * f(r - e) + f(r - 2 * e)) / (12 * h))
+    return out
+
+
+@pytest.mark.parametrize("host", HOSTS)
+def test_incident_field_is_eq22_applied_to_I1(host):
+    """E_inc = i w mu0 (e_z + grad d/dz / k^2) I1 (Eq. 22) with I1 of Eq. 23;
+    d/dz of I1 is i w / v times I1, the transverse gradient is differenced."""
+    eps_h, ekin, e_eV = host
+    v, m_h, beta, gamma, w = _host(eps_h, ekin, e_eV)
+    k = m_h * w / C_LIGHT
+    x0, y0 = 3.0 * NM, -2.0 * NM
+    pts = np.array([[14.0, 5.0, 3.0], [-6.0, 9.0, -11.0], [30.0, -20.0, 7.0]]) * NM
+    for conj, fn in ((False, field.incident_field), (True, field.auxiliary_field)):
+        s = -1.0 if conj else 1.0
+        E = fn(pts, w, v, m_h, gamma, x0, y0)
+        for i, r in enumerate(pts):
+            I1 = lambda rr: field.line_integral_I1(rr[None, :], w, v, gamma, x0, y0, conjugate=conj)[0]
+            b = math.hypot(r[0] - x0, r[1] - y0)
+            gx, gy = _fd_grad_xy(I1, r, 1e-3 * b)
+            dz = s * 1j * w / v
+            ref = 1j * w * MU0 * np.array([dz / k ** 2 * gx, dz / k ** 2 * gy, I1(r) + dz * dz / k ** 2 * I1(r)])
+            assert np.max(np.abs(E[i] - ref)) < 1e-8 * np.max(np.abs(ref)), (conj, host)
+
+
+@pytest.mark.parametrize("host", HOSTS)
+def test_auxiliary_field_second_form_of_eq34(host):
+    eps_h, ekin, e_eV = host
+    v, m_h, beta, gamma, w = _host(eps_h, ekin, e_eV)
+    pts = np.array([[14.0, 5.0, 3.0], [-6.0, 9.0, -11.0]]) * NM
+    E = field.incident_field(pts, w, v, m_h, gamma, 1e-9, 0.0)
+    Ea = field.auxiliary_field(pts, w, v, m_h, gamma, 1e-9, 0.0)
+    ph = np.exp(-2j * w * pts[:, 2] / v)
+    ref = np.stack([-E[:, 0], -E[:, 1], E[:, 2]], axis=1) * ph[:, None]
+    assert np.allclose(Ea, ref, rtol=1e-13, atol=0)
+    # E_a = -E_inc^* exactly when gamma_h is real (Sec. 2.4)
+    same = np.allclose(Ea, -np.conj(E), rtol=1e-12, atol=0)
+    assert same == (gamma.imag == 0.0)
+
+
+def test_quasistatic_limit_eq_S15():
+    v, m_h, beta, gamma, w = _host(2.1025, 100.0, 0.01)
+    eps_h = EPS0 * 2.1025
+    pts = np.array([[2.0, 1.0, 0.5]]) * NM
+    E = field.incident_field(pts, w, v, m_h, gamma, 0.0, 0.0)[0]
+    b2 = (pts[0, 0] ** 2 + pts[0, 1] ** 2)
+    ref = Q_ELECTRON / (2 * np.pi * eps_h * v) * np.exp(1j * w * pts[0, 2] / v) / b2 * np.array([pts[0, 0], pts[0, 1], 0.0])
+    kb = abs(w * math.sqrt(b2) / (gamma * v))
+    # transverse part: K1(x) = 1/x + O(x ln x); E_z ~ K0/gamma_h = O(ln x) is what S15 drops
+    assert np.max(np.abs(E[:2] - ref[:2])) < 2 * kb ** 2 * abs(math.log(kb)) * np.max(np.abs(ref))
+    assert abs(E[2]) < 2 * kb * abs(math.log(kb)) * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------- Green's tensor
+def test_green_tensor_is_eq5_by_finite_differences():
+    rng = np.random.default_rng(1)
+    for k in (2.0e7, 1.3e7 + 2.0e5j, 3.1e7 + 4e6j):
+        for _ in range(3):
+            R = rng.normal(size=3) * 20 * NM
+            phi = lambda x: np.exp(1j * k * np.linalg.norm(x)) / np.linalg.norm(x)
+            h = 1e-3 * np.linalg.norm(R)
+            H = np.zeros((3, 3), dtype=complex)
+            st = [(-2, -1 / 12), (-1, 8 / 12), (1, -8 / 12), (2, 1 / 12)]
+            for a in range(3):
+                for b in range(3):
+                    ea, eb = np.eye(3)[a] * h, np.eye(3)[b] * h
+                    H[a, b] = sum(ca * cb * phi(R - ia * ea - ib * eb) for ia, ca in st for ib, cb in st) / h ** 2
+            ref = k ** 2 * phi(R) * np.eye(3) + H
+            G = green.green_tilde(R, k)
+            assert np.max(np.abs(G - ref)) < 1e-7 * np.max(np.abs(ref))
+
+
+def test_green_tensor_im_part_limit_eq15():
+    k = 1.7e7
+    for rn in (3e-11, 6e-11):     # kR ~ 1e-3: limit error O((kR)^2), cancellation error ~1e-16/(kR)^2
+        G = green.green_tilde(np.array([rn, 0.3 * rn, -0.2 * rn]), k)
+        # Im G = Im G~ / (4 pi k^2) -> k/(6 pi) I
+        assert np.allclose(np.imag(G) / (4 * np.pi * k ** 2), k / (6 * np.pi) * np.eye(3), rtol=1e-5, atol=1e-5 * k / (6 * np.pi))
+
+
+# ---------------------------------------------------------------- assembly / matvec / solve
+def test_dense_matrix_equals_loops_and_is_complex_symmetric():
+    occ = np.array([[[1, 2], [0, 1]], [[2, 1], [1, 0]]], dtype=np.uint8)
+    idx, r, mat = run.lattice(2, 2, 2, 1.5, occ)
+    alpha = np.array([1e-27 * (1 + 0.3j * m) for m in mat])
+    k = 1.2e7 + 3e5j
+    A = green.dense_matrix(r, k, alpha)
+    assert np.allclose(A, green.dense_matrix_loops(r, k, alpha), rtol=1e-14, atol=0)
+    assert np.allclose(A, A.T, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2), (3, 4, 5), (7, 3, 2), (5, 5, 5)])
+def test_fft_operator_equals_dense_matvec(dims):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(sum(dims))
+    occ = (rng.random((nz, ny, nx)) < 0.7).astype(np.uint8)
+    occ.flat[0] = 1
+    idx, r, mat = run.lattice(nx, ny, nz, 2.0, occ)
+    alpha = (1 + 0.2j) * 1e-27 * np.ones(len(r))
+    k = 2.2e7 + 1e6j
+    A = green.dense_matrix(r, k, alpha)
+    op = green.FFTOperator(idx, dims, 2.0 * NM, k, alpha)
+    x = I.random_complex((len(r), 3), seed=7)
+    assert np.allclose(op.matvec(x).reshape(-1), A @ x.reshape(-1), rtol=1e-12, atol=1e-12 * np.abs(A @ x.reshape(-1)).max())
+
+
+def test_krylov_fft_solver_equals_lu_on_small_sphere():
+    w = I.config_small_sphere()
+    pt = run.setup(w.grid.nx, w.grid.ny, w.grid.nz, w.grid.d_nm, w.grid.occ, 2.4, w.eps_p[0], 1.0, (15.0, 0.0), ekin_keV=100.0)
+    p_lu = run.solve_lu(pt)
+    p_k, op = run.solve_fft(pt, rtol=1e-13)
+    assert np.linalg.norm(p_k - p_lu) < 1e-10 * np.linalg.norm(p_lu)
+    assert run.residual(pt, p_lu, op) < 1e-12
+
+
+# ---------------------------------------------------------------- losses
+def test_single_dipole_closed_forms():
+    occ = np.ones((1, 1, 1), dtype=np.uint8)
+    e = 2.2
+    for eps_h in (1.0, 2.1025):
+        o = run.solve_point(1, 1, 1, 4.0, occ, e, [I.drude(e)], eps_h, (10.0, 0.0), ekin_keV=100.0, want_img=True)
+        pt = o["point"]
+        E2 = np.sum(np.abs(pt.E_inc) ** 2)
+        a = pt.alpha[0]
+        k = pt.k.real
+        assert o["P_EELS"] == pytest.approx(4 * EPS0 * eps_h / HBAR ** 2 * np.imag(a) * E2 * E_CHARGE, rel=1e-12)
+        p2 = abs(a) ** 2 * E2
+        p_cl_ref = 8.0 / 3.0 * EPS0 * eps_h * k ** 3 * p2 / HBAR ** 2 * E_CHARGE
+        assert o["P_CL"] == pytest.approx(p_cl_ref, rel=1e-12)       # icosphere is exact for degree <= 5
+        assert o["P_sca_img"] == pytest.approx(p_cl_ref, rel=1e-12)
+        assert o["P_abs"] == pytest.approx(4 * EPS0 * eps_h / HBAR ** 2 * p2 * (-np.imag(1 / pt.alpha_cm[0])) * E_CHARGE, rel=1e-12)
+
+
+def _small_sphere(n=8, diam=16.0):
+    return n, n, n, diam / n, I.sphere_occupancy(n, diam)
+
+
+def test_energy_budget_and_ext_equals_eels_below_threshold():
+    g = _small_sphere()
+    for eps_h, ek, e in ((1.0, 100.0, 2.5), (2.1025, 120.0, 2.1), (1.69, 60.0, 3.2)):
+        o = run.solve_point(*g, e, [I.drude(e)], eps_h, (12.0, 3.0), ekin_keV=ek, want_img=True)
+        assert o["point"].beta_h.real < 1
+        assert o["P_EELS"] == pytest.approx(o["P_ext"], rel=1e-12)                       # Sec. 2.4
+        assert o["P_EELS"] == pytest.approx(o["P_abs"] + o["P_sca_img"], rel=1e-11)      # Sec. 2.6 energy budget
+        assert o["P_CL"] == pytest.approx(o["P_sca_img"], rel=1e-8)                      # far field vs Im-G form
+
+
+def test_lossless_particle_cl_equals_eels():
+    g = _small_sphere()
+    o = run.solve_point(*g, 2.0, [6.25], 1.0, (12.0, 0.0), ekin_keV=100.0, want_img=True)
+    assert o["P_abs"] == 0.0
+    assert o["P_sca_img"] == pytest.approx(o["P_EELS"], rel=1e-11)
+
+
+def test_cherenkov_host_eels_differs_from_extinction():
+    g = _small_sphere(8, 40.0)
+    for eps_h in (4.0, 4.0 + 0.05j):
+        o = run.solve_point(*g, 2.5, [I.drude(2.5, I.DRUDE_AG)], eps_h, (30.0, 0.0), ekin_keV=200.0)
+        assert o["point"].beta_h.real > 1
+        assert abs(o["P_EELS"] - o["P_ext"]) > 1e-3 * abs(o["P_ext"])     # Sec. 3.3, Fig. 8
+        assert o["P_CL"] > 0                                               # Sec. 2.6
+
+
+def test_scale_rule_eq45_vacuum_emulation():
+    g = _small_sphere()
+    m_h = 1.45
+    eps_h = m_h ** 2
+    e, ek = 2.3, 100.0
+    eps_p = I.drude(e)
+    host = run.solve_point(*g, e, [eps_p], eps_h, (12.0, 0.0), ekin_keV=ek)
+    v = physics.electron_speed(ek) * m_h
+    vac = run.solve_point(*g, m_h * e, [eps_p / eps_h], 1.0, (12.0, 0.0), v=v)
+    for key in ("P_EELS", "P_CL", "P_ext", "P_abs"):
+        assert vac[key] == pytest.approx(host[key], rel=1e-10), key
+
+
+def test_scale_rule_eq43_44_general_cherenkov():
+    n, _, _, d, occ = _small_sphere(6, 30.0)
+    eta, xi = 1.3, 0.7
+    eps_h = 4.0 + 0.3j
+    m_h = np.sqrt(eps_h)
+    e, ek = 2.6, 200.0
+    eps_p = I.drude(e, I.DRUDE_AG)
+    v = physics.electron_speed(ek)
+    a = run.solve_point(n, n, n, d, occ, e, [eps_p], eps_h, (25.0, 4.0), v=v)
+    # m_h -> m_h/eta, m_p -> m_p/eta, v -> eta v, r -> r/xi, omega -> xi eta omega; P -> P/xi
+    b = run.solve_point(n, n, n, d / xi, occ, xi * eta * e, [eps_p / eta ** 2], (m_h / eta) ** 2,
+                        (25.0 / xi, 4.0 / xi), v=eta * v)
+    assert a["point"].beta_h.real > 1
+    for key in ("P_EELS", "P_CL", "P_ext", "P_abs"):
+        assert b[key] == pytest.approx(a[key] / xi, rel=1e-10), key
+
+
+# ---------------------------------------------------------------- direction grid
+def test_icosphere_counts_weights_and_low_degree_exactness():
+    V, w = icosphere(4)
+    assert len(V) == 2562 and np.allclose(np.linalg.norm(V, axis=1), 1.0, atol=1e-15)
+    assert w.sum() == pytest.approx(4 * np.pi, rel=1e-14)
+    x, y, z = V.T
+    assert np.sum(w * z * z) == pytest.approx(4 * np.pi / 3, rel=1e-13)
+    assert np.sum(w * x ** 4) == pytest.approx(4 * np.pi / 5, rel=1e-13)
+    assert np.sum(w * x * x * y * y) == pytest.approx(4 * np.pi / 15, rel=1e-13)
+    assert abs(np.sum(w * x * y * z ** 3)) < 1e-13
+    # not exact at degree 6 (so the checks above are not vacuous)
+    assert abs(np.sum(w * x ** 6) - 4 * np.pi / 7) > 1e-9
+
+
+# ---------------------------------------------------------------- Lorenz-Mie
+def test_mie_rayleigh_limit_and_optical_theorem():
+    m = 1.5 + 0.1j
+    k = 1.0e7
+    a = 1e-9
+    ext, sca = mie_cross_sections(m, k, a)
+    ray = 4 * np.pi * k * a ** 3 * np.imag((m * m - 1) / (m * m + 2))
+    assert ext == pytest.approx(ray, rel=1e-3)
+    e2, s2 = mie_cross_sections(1.6 + 0j, k, 50e-9)
+    assert e2 == pytest.approx(s2, rel=1e-12)
+
+
+def test_dda_plane_wave_converges_to_mie():
+    m = 1.5 + 0.1j
+    k = 2 * np.pi / 500e-9
+    diam = 160.0
+    errs = []
+    for n in (6, 10, 14):
+        occ = I.sphere_occupancy(n, diam)
+        d = diam / n
+        nd = int(occ.sum())
+        a_eq = (3 * nd / (4 * np.pi)) ** (1 / 3) * d * NM
+        ext_dda, _ = run.plane_wave_cross_sections(n, n, n, d, occ, m * m, k)
+        ext_mie, _ = mie_cross_sections(m, k, a_eq)
+        errs.append(abs(ext_dda / ext_mie - 1))
+    assert errs[-1] < 0.02
+    assert errs[0] > errs[-1]
+
+
+def test_small_sphere_eels_dipole_limit():
+    """A sphere much smaller than b: the DDA loss tends to the single-dipole
+    loss of the whole sphere, alpha~ = a^3 (m^2-1)/(m^2+2) (radiative
+    reaction included), driven by the field at the centre."""
+    n, diam, b = 10, 4.0, 40.0
+    occ = I.sphere_occupancy(n, diam)
+    e = 3.0
+    eps_p = 2.0 + 1.0j
+    o = run.solve_point(n, n, n, diam / n, occ, e, [eps_p], 1.0, (b, 0.0), ekin_keV=100.0)
+    pt = o["point"]
+    nd = int(occ.sum())
+    a = (3 * nd / (4 * np.pi)) ** (1 / 3) * diam / n * NM
+    a_cm = a ** 3 * (eps_p - 1) / (eps_p + 2)
+    alpha = physics.polarizability_rr(a_cm, pt.k)
+    E0 = field.incident_field(np.zeros((1, 3)), pt.omega, pt.v, pt.m_h, pt.gamma_h, b * NM, 0.0)[0]
+    ref = 4 * EPS0 / HBAR ** 2 * np.imag(alpha) * np.sum(np.abs(E0) ** 2) * E_CHARGE
+    assert o["P_EELS"] == pytest.approx(ref, rel=0.03)
