@@ -1,0 +1,193 @@
+/*
+ * eelsdda.h -- C ABI of the GB300 (sm_103a) discrete-dipole solver for
+ * electron energy-loss (EELS) and cathodoluminescence (CL) probabilities of a
+ * particle in an arbitrary, possibly absorbing or Cherenkov, host medium
+ * (Kichigin & Yurkin, arXiv:2208.01348).
+ *
+ * Problem statement followed (Sec. 2 of the paper):
+ *   - particle: cubic lattice of nx*ny*nz cells of edge d, each empty or filled
+ *     with one of n_mat materials (permittivity eps_p per loss energy);
+ *   - host: relative permittivity eps_h with Im eps_h >= 0 (Sec. 2.1);
+ *   - electron: kinetic energy (keV) along +z through (x0, y0), z0 = 0 (Sec. 2.2,
+ *     Sec. S5);
+ *   - per loss energy hbar*omega and beam: the dipole system
+ *       alpha~_i^-1 p~_i - sum_{j!=i} G~(r_i - r_j) p~_j = E_inc(r_i)
+ *     (point-dipole discretisation of Eq. 8, Green's tensor Eq. 5 with the
+ *     complex host wavenumber k = m_h omega / c, Clausius-Mossotti
+ *     polarizability with radiative reaction, incident field Eq. 25), then
+ *       P_EELS (Eq. 32, 37), P_ext (Eq. 17, 48), P_abs (Eq. 18) and
+ *       P_CL (Eq. 42; far field integrated over the sphere), all in eV^-1.
+ *
+ * Geometry: lattice centred at the origin; cell (ix,iy,iz) has centre
+ * ((ix+1/2) - nx/2) d, ((iy+1/2) - ny/2) d, ((iz+1/2) - nz/2) d.  The
+ * occupancy array is uint8 [nz][ny][nx] (x fastest): 0 empty, k>0 material k.
+ * Dipoles are numbered in that x-fastest order of the occupied cells.
+ *
+ * Units at the boundary: nm, eV, keV; dipole moments p in SI (C m s, the
+ * frequency-domain moment p = 4 pi eps0 eps_h p~).
+ *
+ * Ownership: the caller owns every buffer passed in.  Host inputs are copied
+ * before the call returns; outputs are written only on success (or with
+ * EELS_E_NOT_CONVERGED, see below).  A context owns all device memory it
+ * allocates and frees it in eels_destroy.  Device-pointer entry points
+ * (suffix _dev) read and write caller device memory on the given stream and
+ * return once the work is enqueued (the caller synchronises).
+ *
+ * Errors: every int-returning call returns 0 on success or a negative
+ * EELS_E_* code; eels_last_error(ctx) describes the last failure of that
+ * context (thread-compatible: one thread per context at a time).
+ */
+#ifndef EELSDDA_H
+#define EELSDDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    EELS_OK = 0,
+    EELS_E_INVALID_ARG = -1,   /* bad sizes, d <= 0, Im eps_h < 0 (active host, excluded in Sec. 2.1) */
+    EELS_E_BEAM_INSIDE = -2,   /* trajectory crosses an occupied cell: sources and particle overlap (Sec. 2.1) */
+    EELS_E_THRESHOLD = -3,     /* |1 - beta_h^2| < 1e-12: gamma_h of Eq. 24 is singular */
+    EELS_E_NOT_CONVERGED = -4, /* outputs written; stats flag the unconverged points */
+    EELS_E_OOM = -5,           /* device allocation failed */
+    EELS_E_CUDA = -6,          /* CUDA runtime error */
+    EELS_E_TIMEOUT = -7,       /* a bounded device-side wait expired */
+    EELS_E_NO_GRID = -8,       /* eels_set_grid not called */
+    EELS_E_UNSUPPORTED = -9    /* e.g. padded FFT length outside the supported range */
+};
+
+enum { EELS_FP64 = 0, EELS_MIXED = 1 };          /* precision of the Krylov iterations */
+enum { EELS_QMR = 0, EELS_BICGSTAB = 1 };       /* complex-symmetric Krylov solver */
+
+typedef struct { double re, im; } eels_c128;
+
+typedef struct eels_ctx eels_ctx;
+
+typedef struct {
+    int nx, ny, nz;          /* lattice extents (cells) */
+    double d_nm;             /* cell edge (dipole spacing) */
+    const uint8_t* occ;      /* host, [nz][ny][nx], 0 = empty, k = material k (1-based) */
+} eels_grid;
+
+typedef struct { double x0_nm, y0_nm; } eels_beam;   /* electron along +z, z0 = 0 */
+
+typedef struct {
+    double ekin_keV;         /* electron kinetic energy */
+    int precision;           /* EELS_FP64: FP64 Krylov; EELS_MIXED: FP32 Krylov + FP64 refinement */
+    int solver;              /* EELS_QMR or EELS_BICGSTAB */
+    double eps_it;           /* target relative residual ||b - A x|| / ||b|| (FP64) of the Jacobi-scaled system */
+    double eps_inner;        /* EELS_MIXED: relative residual target of each FP32 inner solve */
+    int max_iter;            /* Krylov iterations per inner solve (and in total for EELS_FP64) */
+    int n_dir;               /* far-field directions: 0 = no CL, else 10*4^L+2 (icosphere level L; 2562 = L4) */
+    int max_batch;           /* (energy, beam) systems solved together; 0 = choose from free memory */
+} eels_opts;
+
+typedef struct {
+    int iters;               /* Krylov iterations (all inner solves) */
+    int refinements;         /* FP64 residual evaluations */
+    double residual;         /* final FP64 relative residual of the Jacobi-scaled system */
+    int converged;           /* 1 if residual <= eps_it */
+} eels_point_stats;
+
+/* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR, eps_it 1e-8,
+ * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0. */
+void eels_default_opts(eels_opts* opts);
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL: the context creates its own non-blocking stream). */
+int eels_create(eels_ctx** out, int device, void* cuda_stream);
+
+/* Free every device allocation of the context (NULL allowed). */
+void eels_destroy(eels_ctx* ctx);
+
+/* Text of the context's last error ("" if none).  Valid until the next call. */
+const char* eels_last_error(const eels_ctx* ctx);
+
+/* Set the particle lattice (copies occ).  Returns EELS_E_INVALID_ARG for
+ * non-positive extents or d, or an empty lattice; EELS_E_UNSUPPORTED if a
+ * padded FFT length (smallest even 7-smooth >= 2n-1 per axis) exceeds 256
+ * (more than 128 cells along an axis). */
+int eels_set_grid(eels_ctx* ctx, const eels_grid* grid);
+
+/* Number of occupied cells of the current grid (dipoles N). */
+int eels_num_dipoles(const eels_ctx* ctx);
+
+/* Padded FFT extents chosen for the current grid. */
+int eels_padded_dims(const eels_ctx* ctx, int* mx, int* my, int* mz);
+
+/*
+ * Solve every (energy, beam) point and reduce the losses.  Host buffers.
+ *   energy_eV [n_energy]; eps_p [n_energy][n_mat] (relative permittivity of
+ *   material k at energy e); eps_h [n_energy]; beams [n_beam].
+ * Outputs ([n_energy][n_beam], eV^-1; any may be NULL except p_eels):
+ *   p_eels (Eq. 37), p_cl (Eq. 42, requires opts->n_dir > 0), p_ext (Eq. 48),
+ *   p_abs (Eq. 18); p_out [n_energy][n_beam][N][3] SI dipoles; stats per point.
+ * Returns EELS_E_NOT_CONVERGED (outputs written) if some point missed eps_it.
+ */
+int eels_solve(eels_ctx* ctx, const eels_opts* opts, int n_energy, const double* energy_eV,
+               int n_mat, const eels_c128* eps_p, const eels_c128* eps_h,
+               int n_beam, const eels_beam* beams,
+               double* p_eels, double* p_cl, double* p_ext, double* p_abs,
+               eels_c128* p_out, eels_point_stats* stats);
+
+/* Device-memory footprint (bytes) eels_solve would allocate for a batch of
+ * n_systems (energy, beam) systems of this grid under these options. */
+int eels_query_footprint(const eels_grid* grid, const eels_opts* opts, int n_systems, size_t* bytes);
+
+/* ------------------------------------------------------------------------
+ * Step-level entry points (parity of individual hot-path steps).
+ * ---------------------------------------------------------------------- */
+
+/* K0(z), K1(z) for complex z (|arg z| < pi), FP64, on the device: z, k0, k1
+ * are DEVICE arrays of n eels_c128 (interleaved re, im).  Enqueued on
+ * cuda_stream (NULL = legacy default stream).  Eq. 25 needs them in the
+ * fourth quadrant (Sec. 2.2); accuracy ~1e-15 relative there. */
+int eels_bessel_k01_dev(const eels_c128* z, eels_c128* k0, eels_c128* k1, int n, void* cuda_stream);
+
+/* Incident field E_inc (Eq. 25) and auxiliary field E_a (Eq. 34) at the
+ * dipoles of the current grid, host outputs [N][3] in V s / m (either may be
+ * NULL).  eps_h relative permittivity; beam at (x0, y0). */
+int eels_incident_field(eels_ctx* ctx, double ekin_keV, double energy_eV, eels_c128 eps_h,
+                        eels_beam beam, eels_c128* e_inc, eels_c128* e_aux);
+
+/* y = A x for the dipole matrix of the current grid, A = diag(alpha~^-1) - G~
+ * in SI (m^-3), x and y host [n_vec][N][3].  precision selects the FP64 or the
+ * FP32 FFT path (the same kernels eels_solve uses).  eps_p [n_mat]. */
+int eels_apply_matrix(eels_ctx* ctx, int precision, double energy_eV, int n_mat, const eels_c128* eps_p,
+                      eels_c128 eps_h, int n_vec, const eels_c128* x, eels_c128* y);
+
+/* Prepare the Jacobi-scaled operator A' = I - a^1/2 G~' a^1/2 (lattice
+ * units: lengths in d, a = alpha~/d^3) for one system per energy, so that
+ * eels_matvec_dev can apply it.  Builds D-hat (FFT of the Green's tensor,
+ * Eq. 5, on the padded lattice) in FP64 and FP32.  Host inputs as in
+ * eels_solve (eps_p [n_energy][n_mat]). */
+int eels_prepare_operator(eels_ctx* ctx, int n_energy, const double* energy_eV, int n_mat, const eels_c128* eps_p,
+                          const eels_c128* eps_h);
+
+/* y = A' x for n_sys prepared systems (n_sys <= n_energy of the last
+ * eels_prepare_operator).  x, y: DEVICE arrays [n_sys][3][N] (component-major
+ * per system) of complex64 (precision EELS_MIXED) or complex128
+ * (EELS_FP64); x and y must not overlap.  Enqueued on cuda_stream (NULL =
+ * legacy default stream); the context's FFT scratch is used, so calls on one
+ * context must not overlap in time.  This is the FFT matrix-vector product
+ * every Krylov iteration applies. */
+int eels_matvec_dev(eels_ctx* ctx, int precision, const void* x, void* y, int n_sys, void* cuda_stream);
+
+/* Kernels launched by this library in this process so far (graph replays
+ * count their kernel nodes). */
+long long eels_kernel_launches(void);
+
+/* The far-field direction grid the CL reduction uses (icosphere with
+ * n_dir = 10*4^L+2 vertices): dirs [n_dir][3] unit vectors, weights
+ * [n_dir] (sum 4 pi).  Host outputs. */
+int eels_directions(int n_dir, double* dirs, double* weights);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EELSDDA_H */

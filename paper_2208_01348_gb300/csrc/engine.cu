@@ -1,0 +1,1001 @@
+// Host engine and C ABI of libeelsdda (see include/eelsdda.h).
+//
+// A solve runs, per batch of (energy, beam) systems (energy-major order):
+//   1. per energy: host scalars omega, m_h, beta_h, gamma_h (Eq. 24), k = m_h k0,
+//      polarizabilities (Clausius-Mossotti with radiative reaction);
+//   2. D-hat: FFT of the Green's tensor (Eq. 5) on the padded lattice (FP64,
+//      also rounded to FP32), one per energy, shared by that energy's beams;
+//   3. incident field (Eq. 25) per (system, dipole), FP64;
+//   4. the Jacobi-scaled system (I - a^1/2 G~ a^1/2) y = a^1/2 E is solved by
+//      FP64 iterative refinement: r = b - A x in FP64, an inner QMR solve of
+//      A d = r (FP32 in EELS_MIXED, FP64 in EELS_FP64), x += d, until
+//      ||r|| <= eps_it ||b||;
+//   5. loss sums (Eq. 32, 17, 18) in FP64 and the CL far field (Eq. 42).
+// Lengths inside are in units of d and fields in units of the modulus of
+// the Eq. 25 prefactor, so FP32 never meets the ~1e-37 magnitudes of SI
+// dipole moments.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <mutex>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/eelsdda.h"
+#include "kernels.h"
+#include "solve.h"
+
+using cd = std::complex<double>;
+using namespace eels;
+
+namespace eels {
+std::atomic<long long> g_kernel_launches{0};
+thread_local bool g_capturing = false;
+}  // namespace eels
+
+namespace {
+
+// Physical constants, SI (CODATA 2018; e, hbar, c exact).
+constexpr double kE = 1.602176634e-19;
+constexpr double kHbar = 1.054571817e-34;
+constexpr double kC = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMeC2keV = 510.99895000;
+constexpr double kPi = 3.14159265358979323846;
+
+struct Fail {
+    int code;
+    std::string msg;
+};
+
+#define CK(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? EELS_E_OOM : EELS_E_CUDA,                   \
+                       std::string(#call) + ": " + cudaGetErrorString(e_)};                          \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    void ensure(size_t n) {
+        if (n <= bytes) return;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (n == 0) return;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            throw Fail{EELS_E_OOM, "cudaMalloc(" + std::to_string(n) + " bytes) failed"};
+        }
+        bytes = n;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+int good_fft_len(int n) {
+    // smallest even 2^a 3^b 5^c 7^d >= 2n - 1 (any M >= 2n - 1 embeds the convolution)
+    int m = std::max(2, 2 * n - 1);
+    for (;; ++m) {
+        if (m & 1) continue;
+        int r = m;
+        for (int p : {2, 3, 5, 7})
+            while (r % p == 0) r /= p;
+        if (r == 1) return m;
+    }
+}
+
+FftPlan make_plan(int L) {
+    FftPlan p{};
+    p.L = L;
+    int r = L;
+    std::vector<int> rad;
+    for (int q : {7, 5, 3}) while (r % q == 0) { rad.push_back(q); r /= q; }
+    while (r % 8 == 0) { rad.push_back(8); r /= 8; }
+    while (r % 4 == 0) { rad.push_back(4); r /= 4; }
+    while (r % 2 == 0) { rad.push_back(2); r /= 2; }
+    // larger radices first reduce the number of passes over shared memory
+    std::sort(rad.begin(), rad.end(), [](int a, int b) { return a > b; });
+    p.nst = (int)rad.size();
+    for (int i = 0; i < p.nst; ++i) p.radix[i] = rad[i];
+    return p;
+}
+
+// Icosphere: level-L subdivided icosahedron, vertex weights = 1/3 of the
+// adjacent spherical-triangle areas (sum 4 pi).
+bool icosphere(int n_dir, std::vector<double>& dirs, std::vector<double>& wts) {
+    int level = -1;
+    for (int l = 0; l <= 7; ++l)
+        if (10 * (1 << (2 * l)) + 2 == n_dir) level = l;
+    if (level < 0) return false;
+    const double t = (1.0 + std::sqrt(5.0)) / 2.0;
+    std::vector<std::array<double, 3>> V = {{-1, t, 0}, {1, t, 0}, {-1, -t, 0}, {1, -t, 0}, {0, -1, t}, {0, 1, t},
+                                            {0, -1, -t}, {0, 1, -t}, {t, 0, -1}, {t, 0, 1}, {-t, 0, -1}, {-t, 0, 1}};
+    for (auto& v : V) {
+        double n = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        for (auto& c : v) c /= n;
+    }
+    std::vector<std::array<int, 3>> F = {{0, 11, 5}, {0, 5, 1}, {0, 1, 7}, {0, 7, 10}, {0, 10, 11}, {1, 5, 9}, {5, 11, 4},
+                                         {11, 10, 2}, {10, 7, 6}, {7, 1, 8}, {3, 9, 4}, {3, 4, 2}, {3, 2, 6}, {3, 6, 8},
+                                         {3, 8, 9}, {4, 9, 5}, {2, 4, 11}, {6, 2, 10}, {8, 6, 7}, {9, 8, 1}};
+    for (int l = 0; l < level; ++l) {
+        std::map<std::pair<int, int>, int> cache;
+        auto mid = [&](int a, int b) {
+            auto key = std::make_pair(std::min(a, b), std::max(a, b));
+            auto it = cache.find(key);
+            if (it != cache.end()) return it->second;
+            std::array<double, 3> m;
+            for (int c = 0; c < 3; ++c) m[c] = V[a][c] + V[b][c];
+            double n = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            for (auto& c : m) c /= n;
+            V.push_back(m);
+            cache[key] = (int)V.size() - 1;
+            return (int)V.size() - 1;
+        };
+        std::vector<std::array<int, 3>> nf;
+        for (auto& f : F) {
+            int ab = mid(f[0], f[1]), bc = mid(f[1], f[2]), ca = mid(f[2], f[0]);
+            nf.push_back({f[0], ab, ca});
+            nf.push_back({f[1], bc, ab});
+            nf.push_back({f[2], ca, bc});
+            nf.push_back({ab, bc, ca});
+        }
+        F.swap(nf);
+    }
+    dirs.assign(3 * V.size(), 0.0);
+    wts.assign(V.size(), 0.0);
+    for (size_t i = 0; i < V.size(); ++i)
+        for (int c = 0; c < 3; ++c) dirs[3 * i + c] = V[i][c];
+    for (auto& f : F) {
+        const auto &a = V[f[0]], &b = V[f[1]], &c = V[f[2]];
+        // solid angle of the spherical triangle (Van Oosterom & Strackee)
+        double bxc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+        double num = std::fabs(a[0] * bxc[0] + a[1] * bxc[1] + a[2] * bxc[2]);
+        double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2], bc = b[0] * c[0] + b[1] * c[1] + b[2] * c[2],
+               ca = c[0] * a[0] + c[1] * a[1] + c[2] * a[2];
+        double om = 2.0 * std::atan2(num, 1.0 + ab + bc + ca);
+        for (int k = 0; k < 3; ++k) wts[f[k]] += om / 3.0;
+    }
+    return true;
+}
+
+double2 d2(cd z) { return make_double2(z.real(), z.imag()); }
+cd cz(eels_c128 z) { return cd(z.re, z.im); }
+
+// Per-energy scalars.
+struct EnergyPar {
+    double omega;
+    cd eps_h, m_h, beta, gamma, k, kappa;
+    double scale;        // |q w / (2 pi eps0 m_h^2 v^2 gamma_h)|
+    cd pref_unit;
+    double wdv;
+    cd alpha[EELS_MAX_MAT], sa[EELS_MAX_MAT], alpha_inv[EELS_MAX_MAT];
+    double wabs[EELS_MAX_MAT];   // -Im 1/alpha'_CM
+};
+
+}  // namespace
+
+struct eels_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    // lattice
+    bool has_grid = false;
+    int nx = 0, ny = 0, nz = 0, N = 0;
+    double d_nm = 0;
+    std::vector<int> cellmap_h, dip_cell_h;
+    std::vector<uint8_t> mat_h;
+    int max_mat = 0;
+    LatticeDev L{};
+    DevBuf cellmap, mat, dip_cell, col_range, tw64[3], tw32[3];
+    // workspace
+    DevBuf e64, b64, x64, r64, y64, U, u64, u32;
+    DevBuf kv[7];                                          // Krylov vectors V0 V1 P0 P1 P2 W X
+    DevBuf part_a, part_b, qmr, active, next_active, counters, outer, res, rnorm;
+    DevBuf sysf, coef, diag, wabs, wdv, slot, kappa_sys;
+    DevBuf G, Dr64, Dr32, kappa_slot;
+    DevBuf lpart, lsums, fpart, fsums, dirs, wts;
+    int dirs_n = 0;
+    int* pinned = nullptr;
+    // cached inner-loop graph
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> graph_key;
+    long long graph_kernels = 0;
+    // operator prepared by eels_prepare_operator
+    int op_systems = 0;
+};
+
+namespace {
+
+void set_err(eels_ctx* c, const std::string& m) {
+    if (c) c->err = m;
+}
+
+template <typename T> void h2d(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    b.ensure(std::max<size_t>(v.size() * sizeof(T), 16));
+    if (!v.empty()) CK(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+void upload_twiddles(eels_ctx* c, int axis, int M) {
+    std::vector<double2> t64(M);
+    std::vector<float2> t32(M);
+    for (int t = 0; t < M; ++t) {
+        // exp(-2 pi i t / M), argument reduced exactly in long double
+        long double a = -2.0L * 3.14159265358979323846264338327950288L * (long double)t / (long double)M;
+        double cr = (double)std::cos(a), ci = (double)std::sin(a);
+        t64[t] = make_double2(cr, ci);
+        t32[t] = make_float2((float)cr, (float)ci);
+    }
+    h2d(c->tw64[axis], t64, c->stream);
+    h2d(c->tw32[axis], t32, c->stream);
+}
+
+void set_grid(eels_ctx* c, const eels_grid* g) {
+    if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->d_nm > 0) || !g->occ)
+        throw Fail{EELS_E_INVALID_ARG, "grid: extents and d must be positive and occ non-NULL"};
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const size_t ncell = (size_t)nx * ny * nz;
+    c->cellmap_h.assign(ncell, -1);
+    c->dip_cell_h.clear();
+    c->mat_h.clear();
+    int maxm = 0;
+    for (size_t i = 0; i < ncell; ++i) {
+        const int m = g->occ[i];
+        if (m == 0) continue;
+        if (m > EELS_MAX_MAT) throw Fail{EELS_E_INVALID_ARG, "grid: material index > 8"};
+        c->cellmap_h[i] = (int)c->dip_cell_h.size();
+        c->dip_cell_h.push_back((int)i);
+        c->mat_h.push_back((uint8_t)(m - 1));
+        maxm = std::max(maxm, m);
+    }
+    if (c->dip_cell_h.empty()) throw Fail{EELS_E_INVALID_ARG, "grid: no occupied cell"};
+    const int Mx = good_fft_len(nx), My = good_fft_len(ny), Mz = good_fft_len(nz);
+    if (Mx > 256 || My > 256 || Mz > 256)
+        throw Fail{EELS_E_UNSUPPORTED, "grid: padded FFT length above 256 (extent above 128 cells)"};
+    std::vector<int2> cr((size_t)nx * ny, make_int2(0, 0));
+    for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix) {
+            int first = -1, last = -1;
+            for (int iz = 0; iz < nz; ++iz)
+                if (c->cellmap_h[((size_t)iz * ny + iy) * nx + ix] >= 0) {
+                    if (first < 0) first = iz;
+                    last = iz;
+                }
+            if (first >= 0) cr[(size_t)iy * nx + ix] = make_int2(first, last + 1);
+        }
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->N = (int)c->dip_cell_h.size();
+    c->d_nm = g->d_nm;
+    c->max_mat = maxm;
+    CK(cudaSetDevice(c->device));
+    h2d(c->cellmap, c->cellmap_h, c->stream);
+    h2d(c->mat, c->mat_h, c->stream);
+    h2d(c->dip_cell, c->dip_cell_h, c->stream);
+    h2d(c->col_range, cr, c->stream);
+    upload_twiddles(c, 0, Mx);
+    upload_twiddles(c, 1, My);
+    upload_twiddles(c, 2, Mz);
+    LatticeDev& L = c->L;
+    L.Nx = nx; L.Ny = ny; L.Nz = nz; L.N = c->N;
+    L.Mx = Mx; L.My = My; L.Mz = Mz;
+    L.Hx = Mx / 2 + 1; L.Hy = My / 2 + 1; L.Hz = Mz / 2 + 1;
+    L.cellmap = c->cellmap.as<int>();
+    L.mat = c->mat.as<uint8_t>();
+    L.dip_cell = c->dip_cell.as<int>();
+    L.col_range = c->col_range.as<int2>();
+    L.px = make_plan(Mx); L.py = make_plan(My); L.pz = make_plan(Mz);
+    L.tw64x = c->tw64[0].as<double2>(); L.tw64y = c->tw64[1].as<double2>(); L.tw64z = c->tw64[2].as<double2>();
+    L.tw32x = c->tw32[0].as<float2>(); L.tw32y = c->tw32[1].as<float2>(); L.tw32z = c->tw32[2].as<float2>();
+    if (matvec_smem_bytes(L, true) == 0) throw Fail{EELS_E_UNSUPPORTED, "grid: FFT tiles do not fit shared memory"};
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_grid = true;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+}
+
+double electron_speed(double ekin_keV) {
+    const double g = 1.0 + ekin_keV / kMeC2keV;
+    return kC * std::sqrt(1.0 - 1.0 / (g * g));
+}
+
+EnergyPar energy_params(double ekin, double e_eV, cd eps_h, int n_mat, const eels_c128* eps_p, double d_m) {
+    if (!(e_eV > 0)) throw Fail{EELS_E_INVALID_ARG, "energies must be positive"};
+    if (eps_h.imag() < 0) throw Fail{EELS_E_INVALID_ARG, "Im eps_h < 0: active host medium (excluded, Sec. 2.1)"};
+    EnergyPar p{};
+    const double v = electron_speed(ekin);
+    p.omega = e_eV * kE / kHbar;
+    p.eps_h = eps_h;
+    p.m_h = std::sqrt(eps_h);                 // principal branch
+    p.beta = v / kC * p.m_h;
+    const cd a = 1.0 - p.beta * p.beta;
+    if (std::abs(a) < 1e-12) throw Fail{EELS_E_THRESHOLD, "|1 - beta_h^2| < 1e-12: gamma_h singular (Eq. 24)"};
+    cd s = (a.imag() == 0.0 && a.real() < 0.0) ? cd(0.0, -std::sqrt(-a.real())) : std::sqrt(a);   // 1/gamma_h
+    p.gamma = 1.0 / s;
+    p.k = p.m_h * p.omega / kC;
+    p.kappa = p.k * d_m;
+    const cd pref = -kE * p.omega / (2.0 * kPi * kEps0 * p.m_h * p.m_h * v * v * p.gamma);
+    p.scale = std::abs(pref);
+    p.pref_unit = pref / p.scale;
+    p.wdv = p.omega * d_m / v;
+    const cd k3 = p.kappa * p.kappa * p.kappa;
+    for (int m = 0; m < n_mat; ++m) {
+        const cd m2 = cz(eps_p[m]) / eps_h;                                     // m^2 = eps_p / eps_h
+        const cd acm = 3.0 / (4.0 * kPi) * (m2 - 1.0) / (m2 + 2.0);           // alpha'_CM = alpha~_CM / d^3
+        const cd al = acm / (1.0 - cd(0.0, 2.0 / 3.0) * k3 * acm);            // radiative reaction
+        p.alpha[m] = al;
+        p.sa[m] = std::sqrt(al);
+        p.alpha_inv[m] = 1.0 / al;
+        p.wabs[m] = -(1.0 / acm).imag();
+    }
+    return p;
+}
+
+void check_beams(eels_ctx* c, int n_beam, const eels_beam* beams) {
+    for (int b = 0; b < n_beam; ++b) {
+        const double x = beams[b].x0_nm / c->d_nm + 0.5 * c->nx, y = beams[b].y0_nm / c->d_nm + 0.5 * c->ny;
+        if (!std::isfinite(x) || !std::isfinite(y)) throw Fail{EELS_E_INVALID_ARG, "beam position not finite"};
+        const int ix = (int)std::floor(x), iy = (int)std::floor(y);
+        // the line crosses a cell (or touches its boundary) whose column holds a dipole
+        for (int jx = ix - 1; jx <= ix + 1; ++jx)
+            for (int jy = iy - 1; jy <= iy + 1; ++jy) {
+                if (jx < 0 || jy < 0 || jx >= c->nx || jy >= c->ny) continue;
+                if (x < jx || x > jx + 1 || y < jy || y > jy + 1) continue;
+                for (int iz = 0; iz < c->nz; ++iz)
+                    if (c->cellmap_h[((size_t)iz * c->ny + jy) * c->nx + jx] >= 0)
+                        throw Fail{EELS_E_BEAM_INSIDE, "beam " + std::to_string(b) + " crosses an occupied cell"};
+            }
+    }
+}
+
+size_t per_system_bytes(const LatticeDev& L, bool fp64) {
+    const size_t n3 = (size_t)3 * L.N;
+    const size_t vec64 = n3 * sizeof(double2);
+    const size_t kvec = n3 * (fp64 ? sizeof(double2) : sizeof(float2));
+    const size_t u = (size_t)3 * L.My * L.Nx * L.Mz * sizeof(double2);
+    const int nblk = (int)((n3 + RED_CHUNK - 1) / RED_CHUNK);
+    return 6 * vec64 + n3 * sizeof(float2) + u + 7 * kvec + 2 * (size_t)nblk * 4 * sizeof(double) + 1024;
+}
+
+size_t per_slot_bytes(const LatticeDev& L) {
+    return (size_t)6 * L.Hx * L.Hy * L.Hz * (sizeof(double2) + sizeof(float2));
+}
+
+struct Batch {
+    int S, e0, e1;   // systems, first/last+1 energy
+};
+
+// ------------------------------------------------------------------ solve
+template <typename Rl>
+KrylovArgs<Rl> krylov_args(eels_ctx* c, int S, const eels_opts* o, double eps) {
+    KrylovArgs<Rl> k{};
+    const int n3 = 3 * c->N;
+    k.S = S;
+    k.n3 = n3;
+    k.nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
+    k.V[0] = c->kv[0].as<cx<Rl>>(); k.V[1] = c->kv[1].as<cx<Rl>>();
+    k.P[0] = c->kv[2].as<cx<Rl>>(); k.P[1] = c->kv[3].as<cx<Rl>>(); k.P[2] = c->kv[4].as<cx<Rl>>();
+    k.W = c->kv[5].as<cx<Rl>>(); k.X = c->kv[6].as<cx<Rl>>();
+    k.part_a = c->part_a.as<double>(); k.part_b = c->part_b.as<double>();
+    k.qmr = c->qmr.as<QmrState>();
+    k.active = c->active.as<int>(); k.next_active = c->next_active.as<int>();
+    k.n_active = c->counters.as<int>();
+    k.eps = eps;
+    k.max_iter = o->max_iter;
+    return k;
+}
+
+template <typename Rl>
+MatvecArgs<Rl> mv_args(eels_ctx* c, int S, const cx<Rl>* x, cx<Rl>* y, const cx<Rl>* Dr, const int* active, bool scaled) {
+    MatvecArgs<Rl> a{};
+    a.x = x; a.y = y; a.U = c->U.as<cx<Rl>>(); a.Dr = Dr;
+    a.sys_slot = c->slot.as<int>();
+    a.coef = c->coef.as<double2>();
+    a.diag = c->diag.as<double2>();
+    a.active = active;
+    a.S = S;
+    (void)scaled;
+    return a;
+}
+
+template <typename Rl> const cx<Rl>* dr_of(eels_ctx* c);
+template <> const float2* dr_of<float>(eels_ctx* c) { return c->Dr32.as<float2>(); }
+template <> const double2* dr_of<double>(eels_ctx* c) { return c->Dr64.as<double2>(); }
+
+// Inner Krylov solve on the active systems; returns the number of iterations run.
+template <typename Rl>
+int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
+    cudaStream_t st = c->stream;
+    KrylovArgs<Rl> k = krylov_args<Rl>(c, S, o, eps);
+    launch_qmr_init<Rl>(k, st);
+    CK(cudaGetLastError());
+    constexpr int CHUNK = 6;   // period of the vector-slot rotation (2 and 3)
+    // every pointer and scalar baked into the captured kernels
+    std::vector<const void*> key = {k.V[0], k.V[1], k.P[0], k.P[1], k.P[2], k.W, k.X, c->U.p, dr_of<Rl>(c),
+                                    (const void*)(size_t)S, (const void*)(size_t)sizeof(Rl),
+                                    (const void*)(size_t)o->max_iter, c->coef.p, c->diag.p, c->slot.p, c->qmr.p,
+                                    c->part_a.p, c->part_b.p, c->active.p, c->next_active.p, c->counters.p,
+                                    c->cellmap.p};
+    // eps is read inside k_qmr_step from the kernel argument: make it part of the key
+    double epsv = eps;
+    const void* ek;
+    std::memcpy(&ek, &epsv, sizeof(ek));
+    key.push_back(ek);
+    if (!c->graph || c->graph_key != key) {
+        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        g_capturing = true;
+        for (int n = 1; n <= CHUNK; ++n) {
+            MatvecArgs<Rl> a = mv_args<Rl>(c, S, k.V[n & 1], k.W, dr_of<Rl>(c), k.active, true);
+            launch_matvec<Rl>(c->L, a, st);
+            launch_qmr_post_matvec<Rl>(k, n, st);
+        }
+        g_capturing = false;
+        CK(cudaStreamEndCapture(st, &g));
+        CK(cudaGraphInstantiate(&c->graph, g, 0));
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        c->graph_kernels = 0;
+        for (auto& nd : nodes) {
+            cudaGraphNodeType ty;
+            cudaGraphNodeGetType(nd, &ty);
+            if (ty == cudaGraphNodeTypeKernel) ++c->graph_kernels;
+        }
+        cudaGraphDestroy(g);
+        c->graph_key = key;
+    }
+    int it = 0;
+    const int max_chunks = o->max_iter / CHUNK + 2;
+    for (int ch = 0; ch < max_chunks; ++ch) {
+        CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*c->pinned <= 0) break;
+        CK(cudaGraphLaunch(c->graph, st));
+        g_kernel_launches += c->graph_kernels;
+        it += CHUNK;
+    }
+    return it;
+}
+
+template <typename Rl>
+void refine_batch(eels_ctx* c, int S, const eels_opts* o, std::vector<int>& iters, std::vector<int>& refin,
+                  std::vector<double>& resid) {
+    cudaStream_t st = c->stream;
+    const int n3 = 3 * c->N;
+    const int nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
+    int* n_outer = c->counters.as<int>() + 1;
+    const double eps_inner = (sizeof(Rl) == 4) ? std::max(o->eps_inner, 1e-7) : std::max(o->eps_it * 0.5, 1e-15);
+    const int max_outer = (sizeof(Rl) == 4) ? 40 : 6;
+    std::vector<QmrState> qh(S);
+    for (int outer_it = 0; outer_it <= max_outer; ++outer_it) {
+        launch_norms2(S, n3, nblk, c->r64.as<double2>(), c->b64.as<double2>(), c->part_a.as<double>(), st);
+        launch_residual_check(S, nblk, c->part_a.as<double>(), o->eps_it, c->res.as<double>(), c->rnorm.as<double>(),
+                              c->outer.as<int>(), n_outer, st);
+        CK(cudaMemcpyAsync(c->pinned, n_outer, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*c->pinned == 0 || outer_it == max_outer) break;
+        launch_make_inner_rhs<Rl>(S, n3, c->r64.as<double2>(), c->rnorm.as<double>(), c->outer.as<int>(),
+                                  c->kv[1].as<cx<Rl>>(), c->active.as<int>(), c->counters.as<int>(), st);
+        inner_qmr<Rl>(c, S, o, eps_inner);
+        CK(cudaMemcpyAsync(qh.data(), c->qmr.p, S * sizeof(QmrState), cudaMemcpyDeviceToHost, st));
+        std::vector<int> outer_h(S);
+        CK(cudaMemcpyAsync(outer_h.data(), c->outer.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+        launch_accumulate<Rl>(S, n3, c->kv[6].as<cx<Rl>>(), c->rnorm.as<double>(), c->outer.as<int>(),
+                              c->x64.as<double2>(), st);
+        MatvecArgs<double> a = mv_args<double>(c, S, c->x64.as<double2>(), c->y64.as<double2>(), c->Dr64.as<double2>(),
+                                               nullptr, true);
+        launch_matvec<double>(c->L, a, st);
+        launch_sub(S, n3, c->b64.as<double2>(), c->y64.as<double2>(), c->r64.as<double2>(), st);
+        CK(cudaStreamSynchronize(st));
+        for (int s = 0; s < S; ++s)
+            if (outer_h[s]) { iters[s] += qh[s].iters; refin[s] += 1; }
+    }
+    CK(cudaMemcpyAsync(resid.data(), c->res.p, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+}
+
+int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* energy_eV, int n_mat,
+               const eels_c128* eps_p, const eels_c128* eps_h, int n_beam, const eels_beam* beams, double* p_eels,
+               double* p_cl, double* p_ext, double* p_abs, eels_c128* p_out, eels_point_stats* stats) {
+    if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+    if (!o || n_energy <= 0 || n_beam <= 0 || !energy_eV || !eps_p || !eps_h || !beams || !p_eels)
+        throw Fail{EELS_E_INVALID_ARG, "solve: NULL input or non-positive counts"};
+    if (n_mat < c->max_mat || n_mat > EELS_MAX_MAT) throw Fail{EELS_E_INVALID_ARG, "n_mat does not cover the grid materials"};
+    if (o->precision != EELS_FP64 && o->precision != EELS_MIXED) throw Fail{EELS_E_INVALID_ARG, "unknown precision"};
+    if (o->solver != EELS_QMR) throw Fail{EELS_E_UNSUPPORTED, "solver: only EELS_QMR is implemented"};
+    if (!(o->eps_it > 0) || o->max_iter <= 0) throw Fail{EELS_E_INVALID_ARG, "eps_it and max_iter must be positive"};
+    if (p_cl && o->n_dir <= 0) throw Fail{EELS_E_INVALID_ARG, "p_cl requested with n_dir = 0"};
+    check_beams(c, n_beam, beams);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t st = c->stream;
+    const LatticeDev& L = c->L;
+    const double d_m = c->d_nm * 1e-9;
+    std::vector<EnergyPar> ep(n_energy);
+    for (int e = 0; e < n_energy; ++e)
+        ep[e] = energy_params(o->ekin_keV, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m);
+    const bool fp64 = o->precision == EELS_FP64;
+    // far-field directions
+    std::vector<double> dirs_h, wts_h;
+    if (p_cl) {
+        if (c->dirs_n != o->n_dir) {
+            if (!icosphere(o->n_dir, dirs_h, wts_h))
+                throw Fail{EELS_E_INVALID_ARG, "n_dir must be 10*4^L+2 (icosphere vertex count)"};
+            h2d(c->dirs, dirs_h, st);
+            h2d(c->wts, wts_h, st);
+            c->dirs_n = o->n_dir;
+        }
+    }
+    // batch size
+    const size_t per_sys = per_system_bytes(L, fp64);
+    const size_t per_slot = per_slot_bytes(L);
+    const size_t Mfull = (size_t)L.Mx * L.My * L.Mz;
+    const size_t gslot = 6 * Mfull * sizeof(double2);
+    int S_max = o->max_batch > 0 ? o->max_batch : 0;
+    if (S_max <= 0) {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        const size_t have = (size_t)(0.6 * (double)(fr + c->U.bytes + c->e64.bytes));
+        S_max = (int)std::max<size_t>(1, have / (per_sys + per_slot + gslot / 8 + 1));
+        S_max = std::min(S_max, 4096);
+    }
+    S_max = std::min(S_max, 21000);
+    const int n_sys = n_energy * n_beam;
+    std::vector<int> iters(n_sys, 0), refin(n_sys, 0);
+    std::vector<double> resid(n_sys, 0.0);
+    bool all_conv = true;
+    for (int s0 = 0; s0 < n_sys; s0 += S_max) {
+        const int S = std::min(S_max, n_sys - s0);
+        const int e0 = s0 / n_beam, e1 = (s0 + S - 1) / n_beam + 1;
+        const int n_slot = e1 - e0;
+        const int n3 = 3 * c->N;
+        const int nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
+        const size_t vec64 = (size_t)S * n3 * sizeof(double2);
+        const size_t kvec = (size_t)S * n3 * (fp64 ? sizeof(double2) : sizeof(float2));
+        c->e64.ensure(vec64); c->b64.ensure(vec64); c->x64.ensure(vec64); c->r64.ensure(vec64);
+        c->y64.ensure(vec64); c->u64.ensure(vec64);
+        c->u32.ensure((size_t)S * n3 * sizeof(float2));
+        c->U.ensure((size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(double2));
+        for (auto& b : c->kv) b.ensure(kvec);
+        c->part_a.ensure((size_t)S * nblk * 4 * sizeof(double));
+        c->part_b.ensure((size_t)S * nblk * 4 * sizeof(double));
+        c->qmr.ensure((size_t)S * sizeof(QmrState));
+        c->active.ensure(S * sizeof(int)); c->next_active.ensure(S * sizeof(int)); c->outer.ensure(S * sizeof(int));
+        c->counters.ensure(64);
+        c->res.ensure(S * sizeof(double)); c->rnorm.ensure(S * sizeof(double));
+        c->Dr64.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(double2));
+        c->Dr32.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(float2));
+        // D-hat for the batch energies, in chunks that fit ~1/8 of the system budget
+        const int gchunk = (int)std::max<size_t>(1, std::min<size_t>(n_slot, (size_t)std::max(1, S) * per_sys / 8 / gslot + 1));
+        c->G.ensure(gchunk * gslot);
+        std::vector<double2> kap_slot(n_slot);
+        for (int e = e0; e < e1; ++e) kap_slot[e - e0] = d2(ep[e].kappa);
+        h2d(c->kappa_slot, kap_slot, st);
+        for (int q0 = 0; q0 < n_slot; q0 += gchunk) {
+            const int nq = std::min(gchunk, n_slot - q0);
+            const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
+            launch_dhat_build(L, nq, c->kappa_slot.as<double2>() + q0, c->G.as<double2>(), c->Dr64.as<double2>() + q0 * hs,
+                              c->Dr32.as<float2>() + q0 * hs, st);
+        }
+        CK(cudaGetLastError());
+        // per-system parameters
+        std::vector<SysField> sf(S);
+        std::vector<double2> coef((size_t)S * EELS_MAX_MAT), diag((size_t)S * EELS_MAX_MAT, make_double2(1, 0));
+        std::vector<double> wabs((size_t)S * EELS_MAX_MAT, 0.0), wdv(S);
+        std::vector<int> slot(S);
+        std::vector<double2> kap(S);
+        for (int s = 0; s < S; ++s) {
+            const int g = s0 + s, e = g / n_beam, b = g % n_beam;
+            const EnergyPar& p = ep[e];
+            sf[s].kt = d2(p.wdv / p.gamma);
+            sf[s].inv_gamma = d2(1.0 / p.gamma);
+            sf[s].pref_unit = d2(p.pref_unit);
+            sf[s].wdv = p.wdv;
+            sf[s].x0 = beams[b].x0_nm / c->d_nm;
+            sf[s].y0 = beams[b].y0_nm / c->d_nm;
+            for (int m = 0; m < EELS_MAX_MAT; ++m) {
+                coef[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? d2(p.sa[m]) : make_double2(0, 0);
+                wabs[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? p.wabs[m] : 0.0;
+            }
+            wdv[s] = p.wdv;
+            slot[s] = e - e0;
+            kap[s] = d2(p.kappa);
+        }
+        h2d(c->sysf, sf, st); h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->wabs, wabs, st);
+        h2d(c->wdv, wdv, st); h2d(c->slot, slot, st); h2d(c->kappa_sys, kap, st);
+        launch_incident_field(L, S, c->sysf.as<SysField>(), c->e64.as<double2>(), st);
+        launch_rhs_init(L, S, c->e64.as<double2>(), c->coef.as<double2>(), c->b64.as<double2>(), c->x64.as<double2>(),
+                        c->r64.as<double2>(), st);
+        CK(cudaGetLastError());
+        std::vector<int> it_b(S, 0), rf_b(S, 0);
+        std::vector<double> rs_b(S, 0.0);
+        if (fp64) refine_batch<double>(c, S, o, it_b, rf_b, rs_b);
+        else refine_batch<float>(c, S, o, it_b, rf_b, rs_b);
+        // losses
+        const int lblk = std::max(1, std::min(64, (c->N + 2047) / 2048));
+        c->lpart.ensure((size_t)S * lblk * 8 * sizeof(double));
+        c->lsums.ensure((size_t)S * 5 * sizeof(double));
+        launch_losses(L, S, c->e64.as<double2>(), c->x64.as<double2>(), c->coef.as<double2>(), c->wabs.as<double>(),
+                      c->wdv.as<double>(), c->lpart.as<double>(), lblk, c->lsums.as<double>(), st);
+        std::vector<double> ls((size_t)S * 5), fs(S, 0.0);
+        CK(cudaMemcpyAsync(ls.data(), c->lsums.p, ls.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (p_cl || p_out)
+            launch_scaled_dipoles(L, S, c->x64.as<double2>(), c->coef.as<double2>(), c->u64.as<double2>(),
+                                  c->u32.as<float2>(), st);
+        if (p_cl) {
+            const int nbf = (o->n_dir + 127) / 128;
+            c->fpart.ensure((size_t)S * nbf * sizeof(double));
+            c->fsums.ensure((size_t)S * sizeof(double));
+            if (fp64)
+                launch_farfield<double>(L, S, c->u64.as<double2>(), c->kappa_sys.as<double2>(), c->dirs.as<double>(),
+                                        c->wts.as<double>(), o->n_dir, c->fpart.as<double>(), c->fsums.as<double>(), st);
+            else
+                launch_farfield<float>(L, S, c->u32.as<float2>(), c->kappa_sys.as<double2>(), c->dirs.as<double>(),
+                                       c->wts.as<double>(), o->n_dir, c->fpart.as<double>(), c->fsums.as<double>(), st);
+            CK(cudaMemcpyAsync(fs.data(), c->fsums.p, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        std::vector<double2> uh;
+        if (p_out) {
+            uh.resize((size_t)S * n3);
+            CK(cudaMemcpyAsync(uh.data(), c->u64.p, uh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        for (int s = 0; s < S; ++s) {
+            const int g = s0 + s, e = g / n_beam;
+            const EnergyPar& p = ep[e];
+            const double d3 = d_m * d_m * d_m;
+            const double f = 4.0 * kEps0 * d3 * p.scale * p.scale / (kHbar * kHbar) * kE;
+            const cd sa(ls[s * 5 + 0], ls[s * 5 + 1]), sx(ls[s * 5 + 2], ls[s * 5 + 3]);
+            p_eels[g] = -f * (p.eps_h * sa).imag();
+            if (p_ext) p_ext[g] = f * (p.eps_h * sx).imag();
+            if (p_abs) p_abs[g] = f * p.eps_h.real() * ls[s * 5 + 4];
+            if (p_cl) {
+                const double ak = std::abs(p.kappa);
+                p_cl[g] = p.m_h.real() * kEps0 * kC * ak * ak * ak * ak * d_m * d_m * p.scale * p.scale * fs[s] /
+                          (kPi * kHbar * kHbar * p.omega) * kE;
+            }
+            if (p_out) {
+                const cd fac = 4.0 * kPi * kEps0 * p.eps_h * d3 * p.scale;
+                for (int i = 0; i < c->N; ++i)
+                    for (int a = 0; a < 3; ++a) {
+                        const double2 u = uh[(size_t)s * n3 + (size_t)a * c->N + i];
+                        const cd v = fac * cd(u.x, u.y);
+                        p_out[((size_t)g * c->N + i) * 3 + a] = {v.real(), v.imag()};
+                    }
+            }
+            const bool conv = rs_b[s] <= o->eps_it;
+            all_conv = all_conv && conv;
+            if (stats) {
+                stats[g].iters = it_b[s];
+                stats[g].refinements = rf_b[s];
+                stats[g].residual = rs_b[s];
+                stats[g].converged = conv ? 1 : 0;
+            }
+        }
+    }
+    return all_conv ? EELS_OK : EELS_E_NOT_CONVERGED;
+}
+
+template <typename F> int guarded(eels_ctx* c, F&& f) {
+    try {
+        if (c) c->err.clear();
+        return f();
+    } catch (const Fail& e) {
+        set_err(c, e.msg);
+        return e.code;
+    } catch (const std::exception& e) {
+        set_err(c, e.what());
+        return EELS_E_CUDA;
+    }
+}
+
+}  // namespace
+
+// =========================================================================
+// C ABI
+// =========================================================================
+extern "C" {
+
+void eels_default_opts(eels_opts* o) {
+    if (!o) return;
+    o->ekin_keV = 100.0;
+    o->precision = EELS_MIXED;
+    o->solver = EELS_QMR;
+    o->eps_it = 1e-8;
+    o->eps_inner = 1e-5;
+    o->max_iter = 20000;
+    o->n_dir = 2562;
+    o->max_batch = 0;
+}
+
+int eels_create(eels_ctx** out, int device, void* cuda_stream) {
+    if (!out) return EELS_E_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return EELS_E_CUDA;
+    }
+    auto* c = new eels_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete c; return EELS_E_CUDA; }
+    // shared-memory opt-in for every kernel instance, once per device and
+    // outside any stream capture
+    static std::mutex mu;
+    static std::vector<int> prepared;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (std::find(prepared.begin(), prepared.end(), device) == prepared.end()) {
+            prepare_kernels();
+            prepared.push_back(device);
+        }
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return EELS_E_CUDA; }
+        c->own_stream = true;
+    }
+    if (cudaMallocHost(&c->pinned, 64) != cudaSuccess) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return EELS_E_OOM;
+    }
+    *out = c;
+    return EELS_OK;
+}
+
+void eels_destroy(eels_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    DevBuf* all[] = {&c->cellmap, &c->mat, &c->dip_cell, &c->col_range, &c->e64, &c->b64, &c->x64, &c->r64, &c->y64,
+                     &c->U, &c->u64, &c->u32, &c->part_a, &c->part_b, &c->qmr, &c->active, &c->next_active,
+                     &c->counters, &c->outer, &c->res, &c->rnorm, &c->sysf, &c->coef, &c->diag, &c->wabs, &c->wdv,
+                     &c->slot, &c->kappa_sys, &c->G, &c->Dr64, &c->Dr32, &c->kappa_slot, &c->lpart, &c->lsums,
+                     &c->fpart, &c->fsums, &c->dirs, &c->wts};
+    for (DevBuf* b : all) b->release();
+    for (auto& b : c->kv) b.release();
+    for (auto& b : c->tw64) b.release();
+    for (auto& b : c->tw32) b.release();
+    if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* eels_last_error(const eels_ctx* c) { return c ? c->err.c_str() : ""; }
+
+int eels_set_grid(eels_ctx* c, const eels_grid* g) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] { set_grid(c, g); return EELS_OK; });
+}
+
+int eels_num_dipoles(const eels_ctx* c) { return (c && c->has_grid) ? c->N : 0; }
+
+int eels_padded_dims(const eels_ctx* c, int* mx, int* my, int* mz) {
+    if (!c || !c->has_grid) return EELS_E_NO_GRID;
+    if (mx) *mx = c->L.Mx;
+    if (my) *my = c->L.My;
+    if (mz) *mz = c->L.Mz;
+    return EELS_OK;
+}
+
+int eels_solve(eels_ctx* c, const eels_opts* o, int n_energy, const double* energy_eV, int n_mat,
+               const eels_c128* eps_p, const eels_c128* eps_h, int n_beam, const eels_beam* beams, double* p_eels,
+               double* p_cl, double* p_ext, double* p_abs, eels_c128* p_out, eels_point_stats* stats) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        return solve_impl(c, o, n_energy, energy_eV, n_mat, eps_p, eps_h, n_beam, beams, p_eels, p_cl, p_ext, p_abs,
+                          p_out, stats);
+    });
+}
+
+int eels_query_footprint(const eels_grid* g, const eels_opts* o, int n_systems, size_t* bytes) {
+    if (!g || !o || !bytes || n_systems <= 0 || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !g->occ) return EELS_E_INVALID_ARG;
+    LatticeDev L{};
+    L.Nx = g->nx; L.Ny = g->ny; L.Nz = g->nz;
+    size_t n = 0;
+    for (size_t i = 0; i < (size_t)g->nx * g->ny * g->nz; ++i) n += g->occ[i] != 0;
+    L.N = (int)n;
+    L.Mx = good_fft_len(g->nx); L.My = good_fft_len(g->ny); L.Mz = good_fft_len(g->nz);
+    L.Hx = L.Mx / 2 + 1; L.Hy = L.My / 2 + 1; L.Hz = L.Mz / 2 + 1;
+    const size_t Mfull = (size_t)L.Mx * L.My * L.Mz;
+    *bytes = (size_t)n_systems * (per_system_bytes(L, o->precision == EELS_FP64) + per_slot_bytes(L)) +
+             6 * Mfull * sizeof(double2) + (size_t)L.Nx * L.Ny * L.Nz * 4 + n * 8;
+    return EELS_OK;
+}
+
+int eels_bessel_k01_dev(const eels_c128* z, eels_c128* k0, eels_c128* k1, int n, void* stream) {
+    if (n < 0 || (n > 0 && (!z || !k0 || !k1))) return EELS_E_INVALID_ARG;
+    launch_bessel(reinterpret_cast<const double2*>(z), reinterpret_cast<double2*>(k0), reinterpret_cast<double2*>(k1), n,
+                  (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? EELS_OK : EELS_E_CUDA;
+}
+
+int eels_incident_field(eels_ctx* c, double ekin_keV, double energy_eV, eels_c128 eps_h, eels_beam beam,
+                        eels_c128* e_inc, eels_c128* e_aux) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+        check_beams(c, 1, &beam);
+        CK(cudaSetDevice(c->device));
+        const double d_m = c->d_nm * 1e-9;
+        eels_c128 one{1.0, 0.0};
+        EnergyPar p = energy_params(ekin_keV, energy_eV, cz(eps_h), 1, &one, d_m);
+        SysField sf;
+        sf.kt = d2(p.wdv / p.gamma); sf.inv_gamma = d2(1.0 / p.gamma); sf.pref_unit = d2(p.pref_unit);
+        sf.wdv = p.wdv; sf.x0 = beam.x0_nm / c->d_nm; sf.y0 = beam.y0_nm / c->d_nm;
+        std::vector<SysField> sv(1, sf);
+        cudaStream_t st = c->stream;
+        h2d(c->sysf, sv, st);
+        const size_t n3 = (size_t)3 * c->N;
+        c->e64.ensure(n3 * sizeof(double2));
+        c->y64.ensure(n3 * sizeof(double2));
+        launch_incident_field(c->L, 1, c->sysf.as<SysField>(), c->e64.as<double2>(), st);
+        launch_aux_field(c->L, 1, c->sysf.as<SysField>(), c->e64.as<double2>(), c->y64.as<double2>(), st);
+        std::vector<double2> h(n3), ha(n3);
+        CK(cudaMemcpyAsync(h.data(), c->e64.p, n3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ha.data(), c->y64.p, n3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        for (int i = 0; i < c->N; ++i)
+            for (int a = 0; a < 3; ++a) {
+                const double2 v = h[(size_t)a * c->N + i], va = ha[(size_t)a * c->N + i];
+                if (e_inc) e_inc[(size_t)i * 3 + a] = {v.x * p.scale, v.y * p.scale};
+                if (e_aux) e_aux[(size_t)i * 3 + a] = {va.x * p.scale, va.y * p.scale};
+            }
+        return EELS_OK;
+    });
+}
+
+int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, const eels_c128* eps_p, eels_c128 eps_h,
+                      int n_vec, const eels_c128* x, eels_c128* y) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+        if (n_vec <= 0 || !x || !y || !eps_p || n_mat < c->max_mat || n_mat > EELS_MAX_MAT)
+            throw Fail{EELS_E_INVALID_ARG, "apply_matrix: bad arguments"};
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = c->stream;
+        const LatticeDev& L = c->L;
+        const double d_m = c->d_nm * 1e-9;
+        EnergyPar p = energy_params(100.0, energy_eV, cz(eps_h), n_mat, eps_p, d_m);
+        const int S = n_vec, n3 = 3 * c->N;
+        const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
+        c->Dr64.ensure(hs * sizeof(double2));
+        c->Dr32.ensure(hs * sizeof(float2));
+        c->G.ensure((size_t)6 * L.Mx * L.My * L.Mz * sizeof(double2));
+        std::vector<double2> ks(1, d2(p.kappa));
+        h2d(c->kappa_slot, ks, st);
+        launch_dhat_build(L, 1, c->kappa_slot.as<double2>(), c->G.as<double2>(), c->Dr64.as<double2>(), c->Dr32.as<float2>(), st);
+        std::vector<double2> coef((size_t)S * EELS_MAX_MAT, make_double2(1, 0)), diag((size_t)S * EELS_MAX_MAT);
+        for (int s = 0; s < S; ++s)
+            for (int m = 0; m < EELS_MAX_MAT; ++m) diag[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? d2(p.alpha_inv[m]) : make_double2(0, 0);
+        std::vector<int> slot(S, 0);
+        h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->slot, slot, st);
+        std::vector<double2> xh((size_t)S * n3);
+        for (int s = 0; s < S; ++s)
+            for (int i = 0; i < c->N; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    const eels_c128 v = x[((size_t)s * c->N + i) * 3 + a];
+                    xh[(size_t)s * n3 + (size_t)a * c->N + i] = make_double2(v.re, v.im);
+                }
+        c->x64.ensure(xh.size() * sizeof(double2));
+        c->y64.ensure(xh.size() * sizeof(double2));
+        c->U.ensure((size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(double2));
+        CK(cudaMemcpyAsync(c->x64.p, xh.data(), xh.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+        std::vector<double2> yh(xh.size());
+        if (precision == EELS_FP64) {
+            MatvecArgs<double> a = mv_args<double>(c, S, c->x64.as<double2>(), c->y64.as<double2>(), c->Dr64.as<double2>(), nullptr, false);
+            launch_matvec<double>(L, a, st);
+            CK(cudaMemcpyAsync(yh.data(), c->y64.p, yh.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        } else {
+            c->u32.ensure(xh.size() * sizeof(float2));
+            c->kv[5].ensure(xh.size() * sizeof(float2));
+            launch_to_f32(xh.size(), c->x64.as<double2>(), c->u32.as<float2>(), st);
+            MatvecArgs<float> a = mv_args<float>(c, S, c->u32.as<float2>(), c->kv[5].as<float2>(), c->Dr32.as<float2>(), nullptr, false);
+            launch_matvec<float>(L, a, st);
+            std::vector<float2> yf(xh.size());
+            CK(cudaMemcpyAsync(yf.data(), c->kv[5].p, yf.size() * sizeof(float2), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (size_t i = 0; i < yf.size(); ++i) yh[i] = make_double2(yf[i].x, yf[i].y);
+        }
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        const double inv_d3 = 1.0 / (d_m * d_m * d_m);
+        for (int s = 0; s < S; ++s)
+            for (int i = 0; i < c->N; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    const double2 v = yh[(size_t)s * n3 + (size_t)a * c->N + i];
+                    y[((size_t)s * c->N + i) * 3 + a] = {v.x * inv_d3, v.y * inv_d3};
+                }
+        return EELS_OK;
+    });
+}
+
+int eels_prepare_operator(eels_ctx* c, int n_energy, const double* energy_eV, int n_mat, const eels_c128* eps_p,
+                          const eels_c128* eps_h) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+        if (n_energy <= 0 || !energy_eV || !eps_p || !eps_h || n_mat < c->max_mat || n_mat > EELS_MAX_MAT)
+            throw Fail{EELS_E_INVALID_ARG, "prepare_operator: bad arguments"};
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = c->stream;
+        const LatticeDev& L = c->L;
+        const double d_m = c->d_nm * 1e-9;
+        const int S = n_energy;
+        const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
+        c->Dr64.ensure(S * hs * sizeof(double2));
+        c->Dr32.ensure(S * hs * sizeof(float2));
+        const size_t gslot = (size_t)6 * L.Mx * L.My * L.Mz * sizeof(double2);
+        c->G.ensure(gslot);
+        std::vector<double2> kap(S), coef((size_t)S * EELS_MAX_MAT), diag((size_t)S * EELS_MAX_MAT, make_double2(1, 0));
+        std::vector<int> slot(S);
+        for (int e = 0; e < S; ++e) {
+            EnergyPar p = energy_params(100.0, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m);
+            kap[e] = d2(p.kappa);
+            slot[e] = e;
+            for (int m = 0; m < EELS_MAX_MAT; ++m) coef[(size_t)e * EELS_MAX_MAT + m] = m < n_mat ? d2(p.sa[m]) : make_double2(0, 0);
+        }
+        h2d(c->kappa_slot, kap, st);
+        for (int e = 0; e < S; ++e)
+            launch_dhat_build(L, 1, c->kappa_slot.as<double2>() + e, c->G.as<double2>(), c->Dr64.as<double2>() + e * hs,
+                              c->Dr32.as<float2>() + e * hs, st);
+        h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->slot, slot, st);
+        c->U.ensure((size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(double2));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        c->op_systems = S;
+        return EELS_OK;
+    });
+}
+
+int eels_matvec_dev(eels_ctx* c, int precision, const void* x, void* y, int n_sys, void* stream) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+        if (n_sys <= 0 || n_sys > c->op_systems || !x || !y)
+            throw Fail{EELS_E_INVALID_ARG, "matvec_dev: n_sys must be in [1, prepared systems]"};
+        cudaStream_t st = (cudaStream_t)stream;
+        if (precision == EELS_FP64) {
+            MatvecArgs<double> a = mv_args<double>(c, n_sys, (const double2*)x, (double2*)y, c->Dr64.as<double2>(), nullptr, true);
+            launch_matvec<double>(c->L, a, st);
+        } else {
+            MatvecArgs<float> a = mv_args<float>(c, n_sys, (const float2*)x, (float2*)y, c->Dr32.as<float2>(), nullptr, true);
+            launch_matvec<float>(c->L, a, st);
+        }
+        CK(cudaGetLastError());
+        return EELS_OK;
+    });
+}
+
+long long eels_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int eels_directions(int n_dir, double* dirs, double* weights) {
+    std::vector<double> d, w;
+    if (!dirs || !weights || !icosphere(n_dir, d, w)) return EELS_E_INVALID_ARG;
+    std::memcpy(dirs, d.data(), d.size() * sizeof(double));
+    std::memcpy(weights, w.data(), w.size() * sizeof(double));
+    return EELS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,415 @@
+// FFT kernels of the DDA matrix-vector product and of the D-hat build.
+//
+// The interaction sum conv(u)_i = sum_{j != i} G~'(r_i - r_j) u_j over a
+// cubic lattice is a 3-D convolution; embedding it in a circulant of
+// extents M >= 2N - 1 per axis turns it into  IFFT( D-hat . FFT(u) ), where
+// D-hat is the FFT of the six symmetric components of G~' on the padded
+// lattice (separation (i - M) for the upper indices, zero at R = 0 and at
+// indices no separation reaches).  The input u is non-zero only on the
+// first Nx x Ny x Nz corner and only that corner of the output is needed, so
+// the forward transform runs z (Nx*Ny lines), then y (Nx*Mz lines), then x
+// (My*Mz lines, fused with the D-hat product and the inverse x transform),
+// and the inverse retraces y then z:  five passes over one scratch array
+// U[s][c][y][x][z] (z fastest), every pass coalesced along z or x.
+//
+// D-hat is stored on the octant 0 <= k <= M/2 only (6 (M/2+1)^3 values):
+// the diagonal components are even in each k and xy, xz, yz are odd in the
+// two axes they name, so D(M - k) = +-D(k).
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace eels {
+
+constexpr int FFT_THREADS = 256;
+
+template <typename Rl> __device__ __forceinline__ const cx<Rl>* tw_of(const LatticeDev& L, int axis);
+template <> __device__ __forceinline__ const double2* tw_of<double>(const LatticeDev& L, int axis) {
+    return axis == 0 ? L.tw64x : (axis == 1 ? L.tw64y : L.tw64z);
+}
+template <> __device__ __forceinline__ const float2* tw_of<float>(const LatticeDev& L, int axis) {
+    return axis == 0 ? L.tw32x : (axis == 1 ? L.tw32y : L.tw32z);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1: scatter the dipole vector onto the lattice (times coef) and
+// transform along z.  Block: W x-adjacent lines at fixed (s, c, iy).
+// ---------------------------------------------------------------------------
+template <typename Rl, int W>
+__global__ void __launch_bounds__(FFT_THREADS) k_zfwd(LatticeDev L, MatvecArgs<Rl> a) {
+    using C = cx<Rl>;
+    const int b = blockIdx.z, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int iy = blockIdx.y, ix0 = blockIdx.x * W;
+    const int Mz = L.Mz, ls = Mz + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* A = tw + Mz;
+    C* B = A + W * ls;
+    const C* twg = tw_of<Rl>(L, 2);
+    for (int t = threadIdx.x; t < Mz; t += blockDim.x) tw[t] = twg[t];
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
+    for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
+        const int w = t % W, iz = t / W, ix = ix0 + w;
+        C v = mk<C>(0.0, 0.0);
+        if (iz < L.Nz && ix < L.Nx) {
+            const int dip = L.cellmap[((size_t)iz * L.Ny + iy) * L.Nx + ix];
+            if (dip >= 0) v = xs[dip] * cvt<C>(cf[L.mat[dip]]);
+        }
+        A[w * ls + iz] = v;
+    }
+    __syncthreads();
+    const C* r = fft_lines<false, false>(A, B, W, ls, 1, L.pz, tw);
+    C* U = a.U + (((size_t)s * 3 + c) * L.My + iy) * (size_t)L.Nx * Mz;
+    for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
+        const int kz = t % Mz, w = t / Mz, ix = ix0 + w;
+        if (ix < L.Nx) U[(size_t)ix * Mz + kz] = r[w * ls + kz];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 5: inverse z transform and gather:  y = diag x - coef conv / M.
+// ---------------------------------------------------------------------------
+template <typename Rl, int W>
+__global__ void __launch_bounds__(FFT_THREADS) k_zinv(LatticeDev L, MatvecArgs<Rl> a, Rl invM) {
+    using C = cx<Rl>;
+    const int b = blockIdx.z, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int iy = blockIdx.y, ix0 = blockIdx.x * W;
+    const int Mz = L.Mz, ls = Mz + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* A = tw + Mz;
+    C* B = A + W * ls;
+    const C* twg = tw_of<Rl>(L, 2);
+    for (int t = threadIdx.x; t < Mz; t += blockDim.x) tw[t] = twg[t];
+    const C* U = a.U + (((size_t)s * 3 + c) * L.My + iy) * (size_t)L.Nx * Mz;
+    for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
+        const int kz = t % Mz, w = t / Mz, ix = ix0 + w;
+        A[w * ls + kz] = ix < L.Nx ? U[(size_t)ix * Mz + kz] : mk<C>(0.0, 0.0);
+    }
+    __syncthreads();
+    const C* r = fft_lines<true, false>(A, B, W, ls, 1, L.pz, tw);
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    C* ys = a.y + ((size_t)s * 3 + c) * L.N;
+    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
+    const double2* dg = a.diag + (size_t)s * EELS_MAX_MAT;
+    for (int t = threadIdx.x; t < W * L.Nz; t += blockDim.x) {
+        const int w = t % W, iz = t / W, ix = ix0 + w;
+        if (ix >= L.Nx) continue;
+        const int dip = L.cellmap[((size_t)iz * L.Ny + iy) * L.Nx + ix];
+        if (dip < 0) continue;
+        const int m = L.mat[dip];
+        const C conv = invM * r[w * ls + iz];
+        ys[dip] = cvt<C>(dg[m]) * xs[dip] - cvt<C>(cf[m]) * conv;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Generic pass along one axis of a batch of arrays [nb][n1][n2][n3].
+// Reads the first in_len entries of every line (zero-extended to the FFT
+// length), writes the first out_len outputs in place.
+// ---------------------------------------------------------------------------
+template <typename Rl, int W, bool INV, int AXIS>
+__global__ void __launch_bounds__(FFT_THREADS) k_axis(cx<Rl>* data, int n1, int n2, int n3, int in_len, int out_len,
+                                                      FftPlan p, const cx<Rl>* twg, const int* active, int per_sys) {
+    using C = cx<Rl>;
+    const int b = blockIdx.z;
+    if (active && !active[b / per_sys]) return;
+    const int Lf = p.L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    for (int t = threadIdx.x; t < Lf; t += blockDim.x) tw[t] = twg[t];
+    if (AXIS == 3) {
+        const int ls = Lf + 1;
+        C* A = tw + Lf;
+        C* B = A + W * ls;
+        const int i1 = blockIdx.y, i20 = blockIdx.x * W;
+        C* base = data + ((size_t)b * n1 + i1) * (size_t)n2 * n3;
+        for (int t = threadIdx.x; t < W * Lf; t += blockDim.x) {
+            const int i = t % Lf, w = t / Lf, i2 = i20 + w;
+            A[w * ls + i] = (i < in_len && i2 < n2) ? base[(size_t)i2 * n3 + i] : mk<C>(0.0, 0.0);
+        }
+        __syncthreads();
+        const C* r = fft_lines<INV, false>(A, B, W, ls, 1, p, tw);
+        for (int t = threadIdx.x; t < W * out_len; t += blockDim.x) {
+            const int i = t % out_len, w = t / out_len, i2 = i20 + w;
+            if (i2 < n2) base[(size_t)i2 * n3 + i] = r[w * ls + i];
+        }
+    } else {
+        const int es = W + 1;
+        C* A = tw + Lf;
+        C* B = A + Lf * es;
+        const int fixed = blockIdx.y, i30 = blockIdx.x * W;
+        size_t base, stride;
+        if (AXIS == 1) { base = (size_t)b * n1 * n2 * n3 + (size_t)fixed * n3; stride = (size_t)n2 * n3; }
+        else { base = ((size_t)b * n1 + fixed) * (size_t)n2 * n3; stride = (size_t)n3; }
+        C* d = data + base;
+        for (int t = threadIdx.x; t < W * Lf; t += blockDim.x) {
+            const int w = t % W, i = t / W, i3 = i30 + w;
+            A[i * es + w] = (i < in_len && i3 < n3) ? d[(size_t)i * stride + i3] : mk<C>(0.0, 0.0);
+        }
+        __syncthreads();
+        const C* r = fft_lines<INV, true>(A, B, W, 1, es, p, tw);
+        for (int t = threadIdx.x; t < W * out_len; t += blockDim.x) {
+            const int w = t % W, i = t / W, i3 = i30 + w;
+            if (i3 < n3) d[(size_t)i * stride + i3] = r[i * es + w];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: forward x transform of the three components, product with the
+// symmetric D-hat tensor, inverse x transform.  Block: W z-adjacent lines
+// at fixed (s, ky); the 3W lines are interleaved in shared memory.
+// ---------------------------------------------------------------------------
+template <typename Rl, int W>
+__global__ void __launch_bounds__(FFT_THREADS) k_xpass(LatticeDev L, MatvecArgs<Rl> a) {
+    using C = cx<Rl>;
+    const int s = blockIdx.z;
+    if (a.active && !a.active[s]) return;
+    const int ky = blockIdx.y, kz0 = blockIdx.x * W;
+    const int Mx = L.Mx, Mz = L.Mz, Nx = L.Nx;
+    constexpr int NL = 3 * W;
+    constexpr int es = NL + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* A = tw + Mx;
+    C* B = A + Mx * es;
+    const C* twg = tw_of<Rl>(L, 0);
+    for (int t = threadIdx.x; t < Mx; t += blockDim.x) tw[t] = twg[t];
+    const size_t plane = (size_t)L.Nx * Mz;
+    C* U0 = a.U + ((size_t)s * 3 * L.My + ky) * plane;
+    const size_t cstride = (size_t)L.My * plane;
+    for (int t = threadIdx.x; t < NL * Mx; t += blockDim.x) {
+        const int l = t % NL, ix = t / NL, c = l / W, w = l % W, kz = kz0 + w;
+        A[ix * es + l] = (ix < Nx && kz < Mz) ? U0[c * cstride + (size_t)ix * Mz + kz] : mk<C>(0.0, 0.0);
+    }
+    __syncthreads();
+    C* r = fft_lines<false, true>(A, B, NL, 1, es, L.px, tw);
+    C* o = (r == A) ? B : A;
+    // D-hat product
+    const int hx = Mx / 2, hy = L.My / 2, hz = Mz / 2;
+    const int kyr = ky <= hy ? ky : L.My - ky;
+    const Rl sy = ky <= hy ? (Rl)1 : (Rl)-1;
+    const size_t cs = (size_t)L.Hy * L.Hx * L.Hz;
+    const C* Ds = a.Dr + (size_t)a.sys_slot[s] * 6 * cs;
+    for (int t = threadIdx.x; t < W * Mx; t += blockDim.x) {
+        const int w = t % W, kx = t / W, kz = kz0 + w;
+        if (kz >= Mz) continue;
+        const int kxr = kx <= hx ? kx : Mx - kx;
+        const int kzr = kz <= hz ? kz : Mz - kz;
+        const Rl sx = kx <= hx ? (Rl)1 : (Rl)-1;
+        const Rl sz = kz <= hz ? (Rl)1 : (Rl)-1;
+        const size_t idx = ((size_t)kyr * L.Hx + kxr) * L.Hz + kzr;
+        const C dxx = Ds[idx], dxy = (sx * sy) * Ds[cs + idx], dxz = (sx * sz) * Ds[2 * cs + idx];
+        const C dyy = Ds[3 * cs + idx], dyz = (sy * sz) * Ds[4 * cs + idx], dzz = Ds[5 * cs + idx];
+        C* e = r + kx * es + w;
+        const C X = e[0], Y = e[W], Z = e[2 * W];
+        e[0] = dxx * X + dxy * Y + dxz * Z;
+        e[W] = dxy * X + dyy * Y + dyz * Z;
+        e[2 * W] = dxz * X + dyz * Y + dzz * Z;
+    }
+    __syncthreads();
+    const C* r2 = fft_lines<true, true>(r, o, NL, 1, es, L.px, tw);
+    for (int t = threadIdx.x; t < NL * Nx; t += blockDim.x) {
+        const int l = t % NL, ix = t / NL, c = l / W, w = l % W, kz = kz0 + w;
+        if (kz < Mz) U0[c * cstride + (size_t)ix * Mz + kz] = r2[ix * es + l];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// D-hat build: G~'(R) on the padded lattice, R in units of d, for n_slot
+// wavenumbers kappa = k d.  Layout G[slot][comp][y][x][z].
+//   G~' = exp(i kappa R)/R [kappa^2 (I - RR) - (1 - i kappa R)/R^2 (I - 3 RR)]   (Eq. 5)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_disp(int i, int n, int m, bool* ok) {
+    if (i < n) return i;
+    if (i > m - n) return i - m;
+    *ok = false;
+    return 0;
+}
+
+__global__ void k_green(LatticeDev L, const double2* kappa, double2* G) {
+    const size_t M = (size_t)L.Mx * L.My * L.Mz;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M) return;
+    const int slot = blockIdx.y;
+    const int z = (int)(idx % L.Mz);
+    const int x = (int)((idx / L.Mz) % L.Mx);
+    const int y = (int)(idx / ((size_t)L.Mz * L.Mx));
+    bool ok = true;
+    const double rx = wrap_disp(x, L.Nx, L.Mx, &ok);
+    const double ry = wrap_disp(y, L.Ny, L.My, &ok);
+    const double rz = wrap_disp(z, L.Nz, L.Mz, &ok);
+    double2 g[6];
+    for (int c = 0; c < 6; ++c) g[c] = make_double2(0.0, 0.0);
+    const double rn2 = rx * rx + ry * ry + rz * rz;
+    if (ok && rn2 > 0.0) {
+        const double rn = sqrt(rn2);
+        const double h[3] = {rx / rn, ry / rn, rz / rn};
+        const double2 kap = kappa[slot];
+        // exp(i kappa R) / R
+        const double2 ikr = make_double2(-kap.y * rn, kap.x * rn);
+        double sn, cs;
+        sincos(ikr.y, &sn, &cs);
+        const double ex = exp(ikr.x) / rn;
+        const double2 ph = make_double2(ex * cs, ex * sn);
+        const double2 k2 = kap * kap;
+        const double2 t = (1.0 / rn2) * make_double2(1.0 - ikr.x, -ikr.y);   // (1 - i kappa R)/R^2
+        const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {0, 1, 2, 1, 2, 2};
+        for (int c = 0; c < 6; ++c) {
+            const double hh = h[pa[c]] * h[pb[c]];
+            const double dd = pa[c] == pb[c] ? 1.0 : 0.0;
+            g[c] = ph * ((dd - hh) * k2 - (dd - 3.0 * hh) * t);
+        }
+    }
+    double2* out = G + (size_t)slot * 6 * M + ((size_t)y * L.Mx + x) * L.Mz + z;
+    for (int c = 0; c < 6; ++c) out[(size_t)c * M] = g[c];
+}
+
+__global__ void k_extract(LatticeDev L, int n_slot, const double2* G, double2* Dr64, float2* Dr32) {
+    const size_t R = (size_t)L.Hx * L.Hy * L.Hz;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * 6 * n_slot) return;
+    const size_t sc = idx / R;          // slot * 6 + comp
+    const size_t r = idx % R;
+    const int kz = (int)(r % L.Hz), kx = (int)((r / L.Hz) % L.Hx), ky = (int)(r / ((size_t)L.Hz * L.Hx));
+    const size_t M = (size_t)L.Mx * L.My * L.Mz;
+    const double2 v = G[sc * M + ((size_t)ky * L.Mx + kx) * L.Mz + kz];
+    Dr64[idx] = v;
+    Dr32[idx] = to_f(v);
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static const size_t kSmemCap = 220 * 1024;
+
+template <typename Rl> static size_t smem_zpass(const LatticeDev& L, int W) { return (size_t)(L.Mz + 2 * W * (L.Mz + 1)) * sizeof(cx<Rl>); }
+template <typename Rl> static size_t smem_xpass(const LatticeDev& L, int W) { return (size_t)(L.Mx + 2 * L.Mx * (3 * W + 1)) * sizeof(cx<Rl>); }
+template <typename Rl> static size_t smem_axis(int Lf, int W, int axis) {
+    return axis == 3 ? (size_t)(Lf + 2 * W * (Lf + 1)) * sizeof(cx<Rl>) : (size_t)(Lf + 2 * Lf * (W + 1)) * sizeof(cx<Rl>);
+}
+
+template <typename K> static void allow_smem(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+}
+
+// Pick the widest tile whose shared memory fits a budget that leaves room
+// for two resident blocks per SM (falling back to one block per SM).
+template <typename F> static int pick_w(F smem_of) {
+    for (int W : {32, 16, 8})
+        if (smem_of(W) <= 110 * 1024) return W;
+    for (int W : {16, 8})
+        if (smem_of(W) <= kSmemCap) return W;
+    return 0;
+}
+
+template <typename Rl, int W, bool INV, int AXIS>
+static void axis_launch_w(cx<Rl>* data, int nb, int n1, int n2, int n3, int in_len, int out_len, const FftPlan& p,
+                          const cx<Rl>* tw, const int* active, int per_sys, cudaStream_t st) {
+    dim3 grid;
+    if (AXIS == 3) grid = dim3((n2 + W - 1) / W, n1, nb);
+    else if (AXIS == 1) grid = dim3((n3 + W - 1) / W, n2, nb);
+    else grid = dim3((n3 + W - 1) / W, n1, nb);
+    count_launch();
+    k_axis<Rl, W, INV, AXIS><<<grid, FFT_THREADS, smem_axis<Rl>(p.L, W, AXIS), st>>>(data, n1, n2, n3, in_len, out_len, p, tw,
+                                                                                    active, per_sys);
+}
+
+template <typename Rl, bool INV, int AXIS>
+static void axis_launch(cx<Rl>* data, int nb, int n1, int n2, int n3, int in_len, int out_len, const FftPlan& p,
+                        const cx<Rl>* tw, const int* active, int per_sys, cudaStream_t st) {
+    const int W = pick_w([&](int w) { return smem_axis<Rl>(p.L, w, AXIS); });
+    if (W == 32) axis_launch_w<Rl, 32, INV, AXIS>(data, nb, n1, n2, n3, in_len, out_len, p, tw, active, per_sys, st);
+    else if (W == 16) axis_launch_w<Rl, 16, INV, AXIS>(data, nb, n1, n2, n3, in_len, out_len, p, tw, active, per_sys, st);
+    else axis_launch_w<Rl, 8, INV, AXIS>(data, nb, n1, n2, n3, in_len, out_len, p, tw, active, per_sys, st);
+}
+
+template <typename Rl> static const cx<Rl>* host_tw(const LatticeDev& L, int axis);
+template <> const double2* host_tw<double>(const LatticeDev& L, int axis) { return axis == 0 ? L.tw64x : (axis == 1 ? L.tw64y : L.tw64z); }
+template <> const float2* host_tw<float>(const LatticeDev& L, int axis) { return axis == 0 ? L.tw32x : (axis == 1 ? L.tw32y : L.tw32z); }
+
+template <typename Rl, int W>
+static void zpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st) {
+    dim3 grid((L.Nx + W - 1) / W, L.Ny, a.S * 3);
+    const size_t sm = smem_zpass<Rl>(L, W);
+    count_launch();
+    if (!inv) k_zfwd<Rl, W><<<grid, FFT_THREADS, sm, st>>>(L, a);
+    else k_zinv<Rl, W><<<grid, FFT_THREADS, sm, st>>>(L, a, (Rl)(1.0 / ((double)L.Mx * L.My * L.Mz)));
+}
+
+template <typename Rl, int W>
+static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+    dim3 grid((L.Mz + W - 1) / W, L.My, a.S);
+    count_launch();
+    k_xpass<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
+}
+
+template <typename Rl>
+void launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+    const int wz = pick_w([&](int w) { return smem_zpass<Rl>(L, w); });
+    if (wz == 32) zpass_launch<Rl, 32>(L, a, false, st);
+    else if (wz == 16) zpass_launch<Rl, 16>(L, a, false, st);
+    else zpass_launch<Rl, 8>(L, a, false, st);
+    axis_launch<Rl, false, 1>(a.U, a.S * 3, L.My, L.Nx, L.Mz, L.Ny, L.My, L.py, host_tw<Rl>(L, 1), a.active, 3, st);
+    const int wx = pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
+    if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
+    else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
+    else xpass_launch<Rl, 8>(L, a, st);
+    axis_launch<Rl, true, 1>(a.U, a.S * 3, L.My, L.Nx, L.Mz, L.My, L.Ny, L.py, host_tw<Rl>(L, 1), a.active, 3, st);
+    if (wz == 32) zpass_launch<Rl, 32>(L, a, true, st);
+    else if (wz == 16) zpass_launch<Rl, 16>(L, a, true, st);
+    else zpass_launch<Rl, 8>(L, a, true, st);
+}
+
+template <typename Rl, int W> static void prepare_w() {
+    allow_smem(k_zfwd<Rl, W>);
+    allow_smem(k_zinv<Rl, W>);
+    allow_smem(k_xpass<Rl, W>);
+    allow_smem(k_axis<Rl, W, false, 1>);
+    allow_smem(k_axis<Rl, W, true, 1>);
+    allow_smem(k_axis<Rl, W, false, 2>);
+    allow_smem(k_axis<Rl, W, false, 3>);
+}
+
+void prepare_far_kernels();
+
+void prepare_kernels() {
+    prepare_w<float, 8>(); prepare_w<float, 16>(); prepare_w<float, 32>();
+    prepare_w<double, 8>(); prepare_w<double, 16>(); prepare_w<double, 32>();
+    prepare_far_kernels();
+}
+
+template void launch_matvec<float>(const LatticeDev&, const MatvecArgs<float>&, cudaStream_t);
+template void launch_matvec<double>(const LatticeDev&, const MatvecArgs<double>&, cudaStream_t);
+
+size_t matvec_smem_bytes(const LatticeDev& L, bool fp64) {
+    if (fp64) {
+        const int wx = pick_w([&](int w) { return smem_xpass<double>(L, w); });
+        const int wz = pick_w([&](int w) { return smem_zpass<double>(L, w); });
+        if (!wx || !wz) return 0;
+        return smem_xpass<double>(L, wx);
+    }
+    const int wx = pick_w([&](int w) { return smem_xpass<float>(L, w); });
+    return wx ? smem_xpass<float>(L, wx) : 0;
+}
+
+void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, double2* G, double2* Dr64, float2* Dr32,
+                       cudaStream_t st) {
+    const size_t M = (size_t)L.Mx * L.My * L.Mz;
+    dim3 g1((unsigned)((M + 255) / 256), n_slot);
+    count_launch();
+    k_green<<<g1, 256, 0, st>>>(L, kappa, G);
+    const int nb = n_slot * 6;
+    axis_launch<double, false, 3>(G, nb, L.My, L.Mx, L.Mz, L.Mz, L.Mz, L.pz, L.tw64z, nullptr, 1, st);
+    axis_launch<double, false, 1>(G, nb, L.My, L.Mx, L.Mz, L.My, L.My, L.py, L.tw64y, nullptr, 1, st);
+    axis_launch<double, false, 2>(G, nb, L.My, L.Mx, L.Mz, L.Mx, L.Mx, L.px, L.tw64x, nullptr, 1, st);
+    const size_t R = (size_t)L.Hx * L.Hy * L.Hz * 6 * n_slot;
+    count_launch();
+    k_extract<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(L, n_slot, G, Dr64, Dr32);
+}
+
+}  // namespace eels

@@ -1,0 +1,486 @@
+// Krylov iterations, FP64 refinement vectors and the loss reductions.
+//
+// QMR for complex-symmetric matrices (Freund, SIAM J. Sci. Stat. Comput. 13
+// (1992) 425), the solver family the paper uses (Sec. S5).  The Lanczos
+// process runs with the unconjugated bilinear form x^T y (the DDA matrix is
+// complex symmetric, A = A^T) on unit-norm vectors:
+//   w = A v_n,  alpha_n = v_n^T w / delta_n,  v~ = w - alpha_n v_n - beta_n v_{n-1},
+//   rho_{n+1} = ||v~||,  v_{n+1} = v~ / rho_{n+1},  delta_{n+1} = v_{n+1}^T v_{n+1},
+//   beta_{n+1} = rho_{n+1} delta_{n+1} / delta_n,
+// and the quasi-residual ||rho_1 e_1 - H_n z|| is minimised with Givens
+// rotations of the tridiagonal H_n (columns (beta_n, alpha_n, rho_{n+1})):
+//   theta = s_{n-2} beta_n, eta = c_{n-1} c_{n-2} beta_n + s_{n-1} alpha_n,
+//   mu = -conj(s_{n-1}) c_{n-2} beta_n + c_{n-1} alpha_n,
+//   c_n = |mu| / r, s_n = (mu/|mu|) rho_{n+1} / r, r_n = (mu/|mu|) r,
+//   r = sqrt(|mu|^2 + rho_{n+1}^2),  t_n = c_n tau_n,  tau_{n+1} = -conj(s_n) tau_n,
+//   p_n = (v_n - eta p_{n-1} - theta p_{n-2}) / r_n,  x_n = x_{n-1} + t_n p_n.
+// The iteration stops when |tau_{n+1}| <= eps ||b||.
+//
+// Every reduction is two-level and deterministic: a fixed grid of blocks
+// per system (independent of how many systems share a launch) writes
+// partial sums; consumers add them in block order.  Partial sums of FP32
+// vectors are accumulated in FP32 inside a block.
+#include <algorithm>
+
+#include "solve.h"
+
+namespace eels {
+
+// --------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums K values over the block; result valid in thread 0.
+template <typename T, int K>
+__device__ __forceinline__ void block_sum(T (&v)[K]) {
+    __shared__ T sh[32 * K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+        for (int k = 0; k < K; ++k) sh[wid * K + k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            T t = lane < nw ? sh[lane * K + k] : (T)0;
+            v[k] = warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+// part[s][blk][0..3] = (Re sum a.b, Im sum a.b, sum |a|^2, sum |b|^2)   (a.b unconjugated)
+template <typename Rl>
+__global__ void k_dot(int n3, int nblk, const cx<Rl>* __restrict__ a, const cx<Rl>* __restrict__ b, double* part,
+                      const int* active) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    if (active && !active[s]) return;
+    const size_t off = (size_t)s * n3;
+    const int i0 = blk * RED_CHUNK, i1 = min(n3, i0 + RED_CHUNK);
+    Rl v[4] = {0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const cx<Rl> x = a[off + i], y = b[off + i];
+        v[0] += x.x * y.x - x.y * y.y;
+        v[1] += x.x * y.y + x.y * y.x;
+        v[2] += x.x * x.x + x.y * x.y;
+        v[3] += y.x * y.x + y.y * y.y;
+    }
+    block_sum<Rl, 4>(v);
+    if (threadIdx.x == 0) {
+        double* p = part + ((size_t)s * nblk + blk) * 4;
+        p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = v[3];
+    }
+}
+
+__device__ __forceinline__ void sum_parts(const double* part, int s, int nblk, double (&o)[4]) {
+    o[0] = o[1] = o[2] = o[3] = 0.0;
+    const double* p = part + (size_t)s * nblk * 4;
+    for (int b = 0; b < nblk; ++b) {
+        o[0] += p[4 * b]; o[1] += p[4 * b + 1]; o[2] += p[4 * b + 2]; o[3] += p[4 * b + 3];
+    }
+}
+
+// ------------------------------------------------------------------- QMR
+template <typename Rl>
+__global__ void k_qmr_start(KrylovArgs<Rl> k) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.S) return;
+    if (!k.active[s]) { k.next_active[s] = 0; return; }
+    double o[4];
+    sum_parts(k.part_a, s, k.nblk, o);     // (b.b, |b|^2)
+    QmrState q;
+    const double rho = sqrt(o[2]);
+    q.bnorm = rho;
+    q.beta = make_double2(0, 0);
+    q.c1 = q.c2 = 1.0;
+    q.s1 = q.s2 = make_double2(0, 0);
+    q.tau = make_double2(rho, 0);
+    q.iters = 0;
+    q.qres = 1.0;
+    q.eta = q.theta = q.t = make_double2(0, 0);
+    q.rinv = make_double2(0, 0);
+    if (rho > 0.0) {
+        q.inv_rho = 1.0 / rho;
+        q.delta = make_double2(o[0] / (rho * rho), o[1] / (rho * rho));
+        q.status = 0;
+        k.next_active[s] = 1;
+    } else {
+        q.inv_rho = 0.0;
+        q.delta = make_double2(1, 0);
+        q.status = 1;
+        q.qres = 0.0;
+        k.next_active[s] = 0;
+    }
+    k.qmr[s] = q;
+}
+
+// v_1 = b / rho_1; zero v_0, p slots and x
+template <typename Rl>
+__global__ void k_qmr_scale(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y;
+    if (!k.active[s]) return;
+    const Rl ir = (Rl)k.qmr[s].inv_rho;
+    const size_t off = (size_t)s * k.n3;
+    const cx<Rl> z = mk<cx<Rl>>(0.0, 0.0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x) {
+        k.V[1][off + i] = ir * k.V[1][off + i];
+        k.V[0][off + i] = z;
+        k.P[0][off + i] = z; k.P[1][off + i] = z; k.P[2][off + i] = z;
+        k.X[off + i] = z;
+    }
+}
+
+// v~ = w - alpha v_n - beta_n v_{n-1}  (into W); partial sums of v~.v~ and |v~|^2
+template <typename Rl>
+__global__ void k_lanczos(KrylovArgs<Rl> k, int n) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    if (!k.active[s]) return;
+    __shared__ double2 sc[2];
+    if (threadIdx.x == 0) {
+        double o[4];
+        sum_parts(k.part_a, s, k.nblk, o);
+        const QmrState& q = k.qmr[s];
+        sc[0] = cdiv(make_double2(o[0], o[1]), q.delta);
+        sc[1] = q.beta;
+    }
+    __syncthreads();
+    const cx<Rl> al = cvt<cx<Rl>>(sc[0]), be = cvt<cx<Rl>>(sc[1]);
+    const cx<Rl>* v = k.V[n & 1];
+    const cx<Rl>* vp = k.V[(n + 1) & 1];
+    const size_t off = (size_t)s * k.n3;
+    const int i0 = blk * RED_CHUNK, i1 = min(k.n3, i0 + RED_CHUNK);
+    Rl acc[4] = {0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const cx<Rl> t = k.W[off + i] - al * v[off + i] - be * vp[off + i];
+        k.W[off + i] = t;
+        acc[0] += t.x * t.x - t.y * t.y;
+        acc[1] += 2 * t.x * t.y;
+        acc[2] += t.x * t.x + t.y * t.y;
+    }
+    block_sum<Rl, 4>(acc);
+    if (threadIdx.x == 0) {
+        double* p = k.part_b + ((size_t)s * k.nblk + blk) * 4;
+        p[0] = acc[0]; p[1] = acc[1]; p[2] = acc[2]; p[3] = 0.0;
+    }
+}
+
+template <typename Rl>
+__global__ void k_qmr_step(KrylovArgs<Rl> k) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.S) return;
+    if (!k.active[s]) { k.next_active[s] = 0; return; }
+    QmrState q = k.qmr[s];
+    double oa[4], ob[4];
+    sum_parts(k.part_a, s, k.nblk, oa);
+    sum_parts(k.part_b, s, k.nblk, ob);
+    const double2 alpha = cdiv(make_double2(oa[0], oa[1]), q.delta);
+    const double rho_n = sqrt(ob[2]);
+    // Givens: apply rotations n-2, n-1 to the column (beta_n, alpha_n, rho_{n+1})
+    const double2 theta = q.s2 * q.beta;
+    const double2 tmp = q.c2 * q.beta;
+    const double2 eta = q.c1 * tmp + q.s1 * alpha;
+    const double2 mu = q.c1 * alpha - conj_(q.s1) * tmp;
+    const double amu = cabs_(mu);
+    double c;
+    double2 sn, r;
+    if (amu == 0.0) {
+        c = 0.0; sn = make_double2(1, 0); r = make_double2(rho_n, 0);
+    } else {
+        const double ra = hypot(amu, rho_n);
+        const double2 ph = (1.0 / amu) * mu;
+        c = amu / ra; sn = (rho_n / ra) * ph; r = ra * ph;
+    }
+    q.theta = theta;
+    q.eta = eta;
+    q.rinv = cdiv(make_double2(1, 0), r);
+    q.t = c * q.tau;
+    q.tau = -(conj_(sn) * q.tau);
+    q.c2 = q.c1; q.s2 = q.s1; q.c1 = c; q.s1 = sn;
+    q.iters += 1;
+    q.qres = cabs_(q.tau) / q.bnorm;
+    int next = 1;
+    if (rho_n > 0.0) {
+        const double2 dn = make_double2(ob[0] / (rho_n * rho_n), ob[1] / (rho_n * rho_n));
+        q.beta = cdiv(rho_n * dn, q.delta);
+        q.inv_rho = 1.0 / rho_n;
+        if (cabs_(dn) < 1e-30) { q.status = 3; next = 0; }
+        q.delta = dn;
+    } else {
+        q.inv_rho = 0.0;           // invariant subspace reached: the update below is exact
+        q.status = 1; next = 0;
+    }
+    if (next && q.qres <= k.eps) { q.status = 1; next = 0; }
+    if (next && q.iters >= k.max_iter) { q.status = 2; next = 0; }
+    if (!(q.qres == q.qres)) { q.status = 3; next = 0; }   // NaN guard
+    k.qmr[s] = q;
+    k.next_active[s] = next;
+}
+
+// p_n = (v_n - eta p_{n-1} - theta p_{n-2}) / r_n ; x += t p_n ; v_{n+1} = v~ / rho_{n+1}
+template <typename Rl>
+__global__ void k_qmr_update(KrylovArgs<Rl> k, int n) {
+    const int s = blockIdx.y;
+    if (!k.active[s]) return;
+    using C = cx<Rl>;
+    const QmrState& q = k.qmr[s];
+    const C eta = cvt<C>(q.eta), th = cvt<C>(q.theta), ri = cvt<C>(q.rinv), t = cvt<C>(q.t);
+    const Rl ir = (Rl)q.inv_rho;
+    const C* v = k.V[n & 1];
+    C* vn = k.V[(n + 1) & 1];
+    C* pn = k.P[n % 3];
+    const C* p1 = k.P[(n + 2) % 3];
+    const C* p2 = k.P[(n + 1) % 3];
+    const size_t off = (size_t)s * k.n3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x) {
+        const C p = ri * (v[off + i] - eta * p1[off + i] - th * p2[off + i]);
+        pn[off + i] = p;
+        k.X[off + i] = k.X[off + i] + t * p;
+        vn[off + i] = ir * k.W[off + i];
+    }
+}
+
+__global__ void k_commit(int S, int* active, const int* next_active, int* n_active) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    if (active[s] && !next_active[s]) {
+        active[s] = 0;
+        atomicSub(n_active, 1);
+    }
+}
+
+static inline dim3 vec_grid(int n3, int S) {
+    int bx = (n3 + 1023) / 1024;
+    if (bx > 64) bx = 64;
+    return dim3(bx, S);
+}
+
+template <typename Rl>
+void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
+    count_launch();
+    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.V[1], k.V[1], k.part_a, k.active);
+    count_launch();
+    k_qmr_start<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    count_launch();
+    k_qmr_scale<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
+    count_launch();
+    k_commit<<<(k.S + 127) / 128, 128, 0, st>>>(k.S, k.active, k.next_active, k.n_active);
+}
+
+template <typename Rl>
+void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, cudaStream_t st) {
+    count_launch();
+    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.V[n & 1], k.W, k.part_a, k.active);
+    count_launch();
+    k_lanczos<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k, n);
+    count_launch();
+    k_qmr_step<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    count_launch();
+    k_qmr_update<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k, n);
+    count_launch();
+    k_commit<<<(k.S + 127) / 128, 128, 0, st>>>(k.S, k.active, k.next_active, k.n_active);
+}
+
+template void launch_qmr_init<float>(const KrylovArgs<float>&, cudaStream_t);
+template void launch_qmr_init<double>(const KrylovArgs<double>&, cudaStream_t);
+template void launch_qmr_post_matvec<float>(const KrylovArgs<float>&, int, cudaStream_t);
+template void launch_qmr_post_matvec<double>(const KrylovArgs<double>&, int, cudaStream_t);
+
+void launch_commit(int S, int* active, const int* next_active, int* n_active, cudaStream_t st) {
+    count_launch();
+    k_commit<<<(S + 127) / 128, 128, 0, st>>>(S, active, next_active, n_active);
+}
+
+// ------------------------------------------------------- FP64 refinement
+__global__ void k_rhs_init(LatticeDev L, int S, const double2* e, const double2* coef, double2* b, double2* x, double2* r) {
+    const int s = blockIdx.y;
+    const size_t n3 = (size_t)3 * L.N, off = (size_t)s * n3;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const int dip = (int)(i % L.N);
+        const double2 v = coef[(size_t)s * EELS_MAX_MAT + L.mat[dip]] * e[off + i];
+        b[off + i] = v;
+        r[off + i] = v;
+        x[off + i] = make_double2(0, 0);
+    }
+}
+
+__global__ void k_norms2(int n3, int nblk, const double2* a, const double2* b, double* part) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    const size_t off = (size_t)s * n3;
+    const int i0 = blk * RED_CHUNK, i1 = min(n3, i0 + RED_CHUNK);
+    double v[2] = {0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        v[0] += abs2_(a[off + i]);
+        v[1] += abs2_(b[off + i]);
+    }
+    block_sum<double, 2>(v);
+    if (threadIdx.x == 0) {
+        double* p = part + ((size_t)s * nblk + blk) * 4;
+        p[0] = v[0]; p[1] = v[1]; p[2] = 0; p[3] = 0;
+    }
+}
+
+__global__ void k_residual_check(int S, int nblk, const double* part, double eps, double* res, double* rnorm, int* outer,
+                                 int* n_outer) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double o[4];
+    sum_parts(part, s, nblk, o);
+    const double rn = sqrt(o[0]), bn = sqrt(o[1]);
+    const double r = bn > 0 ? rn / bn : 0.0;
+    res[s] = r;
+    rnorm[s] = rn;
+    const int go = (r > eps) && (rn > 0.0) && (r == r);
+    outer[s] = go;
+    if (go) atomicAdd(n_outer, 1);
+}
+
+template <typename Rl>
+__global__ void k_make_inner_rhs(int S, int n3, const double2* r, const double* rnorm, const int* outer, cx<Rl>* v,
+                                 int* active, int* n_active) {
+    const int s = blockIdx.y;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        active[s] = outer[s];
+        if (outer[s]) atomicAdd(n_active, 1);
+    }
+    if (!outer[s]) return;
+    const double ir = 1.0 / rnorm[s];
+    const size_t off = (size_t)s * n3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x)
+        v[off + i] = cvt<cx<Rl>>(ir * r[off + i]);
+}
+
+template <typename Rl>
+__global__ void k_accumulate(int S, int n3, const cx<Rl>* xi, const double* rnorm, const int* outer, double2* x) {
+    const int s = blockIdx.y;
+    if (!outer[s]) return;
+    const double rn = rnorm[s];
+    const size_t off = (size_t)s * n3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x)
+        x[off + i] = x[off + i] + rn * widen(xi[off + i]);
+}
+
+__global__ void k_sub(size_t n, const double2* b, const double2* y, double2* r) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        r[i] = b[i] - y[i];
+}
+
+__global__ void k_to_f32(size_t n, const double2* a, float2* b) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = to_f(a[i]);
+}
+
+void launch_rhs_init(const LatticeDev& L, int S, const double2* e, const double2* coef, double2* b, double2* x,
+                     double2* r, cudaStream_t st) {
+    count_launch();
+    k_rhs_init<<<vec_grid(3 * L.N, S), 256, 0, st>>>(L, S, e, coef, b, x, r);
+}
+void launch_norms2(int S, int n3, int nblk, const double2* a, const double2* b, double* part, cudaStream_t st) {
+    count_launch();
+    k_norms2<<<dim3(nblk, S), RED_THREADS, 0, st>>>(n3, nblk, a, b, part);
+}
+void launch_residual_check(int S, int nblk, const double* part, double eps, double* res, double* rnorm, int* outer,
+                           int* n_outer, cudaStream_t st) {
+    cudaMemsetAsync(n_outer, 0, sizeof(int), st);
+    count_launch();
+    k_residual_check<<<(S + 127) / 128, 128, 0, st>>>(S, nblk, part, eps, res, rnorm, outer, n_outer);
+}
+template <typename Rl>
+void launch_make_inner_rhs(int S, int n3, const double2* r, const double* rnorm, const int* outer, cx<Rl>* v,
+                           int* active, int* n_active, cudaStream_t st) {
+    cudaMemsetAsync(n_active, 0, sizeof(int), st);
+    count_launch();
+    k_make_inner_rhs<Rl><<<vec_grid(n3, S), 256, 0, st>>>(S, n3, r, rnorm, outer, v, active, n_active);
+}
+template <typename Rl>
+void launch_accumulate(int S, int n3, const cx<Rl>* xi, const double* rnorm, const int* outer, double2* x,
+                       cudaStream_t st) {
+    count_launch();
+    k_accumulate<Rl><<<vec_grid(n3, S), 256, 0, st>>>(S, n3, xi, rnorm, outer, x);
+}
+template void launch_make_inner_rhs<float>(int, int, const double2*, const double*, const int*, float2*, int*, int*, cudaStream_t);
+template void launch_make_inner_rhs<double>(int, int, const double2*, const double*, const int*, double2*, int*, int*, cudaStream_t);
+template void launch_accumulate<float>(int, int, const float2*, const double*, const int*, double2*, cudaStream_t);
+template void launch_accumulate<double>(int, int, const double2*, const double*, const int*, double2*, cudaStream_t);
+
+void launch_sub(int S, int n3, const double2* b, const double2* y, double2* r, cudaStream_t st) {
+    const size_t n = (size_t)S * n3;
+    count_launch();
+    k_sub<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(n, b, y, r);
+}
+void launch_to_f32(size_t n, const double2* a, float2* b, cudaStream_t st) {
+    count_launch();
+    k_to_f32<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(n, a, b);
+}
+
+// ------------------------------------------------------------ losses
+// Per block partial sums over dipoles: sum E_a.u (3 comps), sum conj(E).u, sum |u|^2 w.
+// E_a = (-E_x, -E_y, E_z) exp(-2 i w (z - z0)/v)   (Eq. 34, second form)
+__global__ void k_losses(LatticeDev L, const double2* e, const double2* x, const double2* coef, const double* wabs,
+                         const double* wdv, double* part, int nblk) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    const size_t N = (size_t)L.N, off = (size_t)s * 3 * N;
+    const int chunk = (L.N + nblk - 1) / nblk;
+    const int i0 = blk * chunk, i1 = min(L.N, i0 + chunk);
+    const double w = wdv[s];
+    double v[5] = {0, 0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int m = L.mat[i];
+        const double2 cf = coef[(size_t)s * EELS_MAX_MAT + m];
+        const double2 ux = cf * x[off + i], uy = cf * x[off + N + i], uz = cf * x[off + 2 * N + i];
+        const double2 ex = e[off + i], ey = e[off + N + i], ez = e[off + 2 * N + i];
+        const int iz = L.dip_cell[i] / (L.Nx * L.Ny);
+        const double zr = (iz + 0.5) - 0.5 * L.Nz;
+        double sn, cs;
+        sincos(-2.0 * w * zr, &sn, &cs);
+        const double2 ph = make_double2(cs, sn);
+        const double2 ea = ph * (ez * uz - ex * ux - ey * uy);
+        const double2 ec = conj_(ex) * ux + conj_(ey) * uy + conj_(ez) * uz;
+        v[0] += ea.x; v[1] += ea.y; v[2] += ec.x; v[3] += ec.y;
+        v[4] += (abs2_(ux) + abs2_(uy) + abs2_(uz)) * wabs[(size_t)s * EELS_MAX_MAT + m];
+    }
+    block_sum<double, 5>(v);
+    if (threadIdx.x == 0) {
+        double* p = part + ((size_t)s * nblk + blk) * 8;
+        for (int q = 0; q < 5; ++q) p[q] = v[q];
+    }
+}
+
+__global__ void k_sum_parts(int S, int nblk, int stride, int nval, const double* part, double* out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    for (int q = 0; q < nval; ++q) {
+        double a = 0.0;
+        for (int b = 0; b < nblk; ++b) a += part[((size_t)s * nblk + b) * stride + q];
+        out[(size_t)s * nval + q] = a;
+    }
+}
+
+void launch_losses(const LatticeDev& L, int S, const double2* e, const double2* x, const double2* coef,
+                   const double* wabs, const double* wdv, double* part, int nblk, double* sums, cudaStream_t st) {
+    count_launch();
+    k_losses<<<dim3(nblk, S), 256, 0, st>>>(L, e, x, coef, wabs, wdv, part, nblk);
+    count_launch();
+    k_sum_parts<<<(S + 127) / 128, 128, 0, st>>>(S, nblk, 8, 5, part, sums);
+}
+
+__global__ void k_scaled_dipoles(LatticeDev L, int S, const double2* x, const double2* coef, double2* u64, float2* u32) {
+    const int s = blockIdx.y;
+    const size_t n3 = (size_t)3 * L.N, off = (size_t)s * n3;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 u = coef[(size_t)s * EELS_MAX_MAT + L.mat[i % L.N]] * x[off + i];
+        if (u64) u64[off + i] = u;
+        if (u32) u32[off + i] = to_f(u);
+    }
+}
+void launch_scaled_dipoles(const LatticeDev& L, int S, const double2* x, const double2* coef, double2* u64, float2* u32,
+                           cudaStream_t st) {
+    count_launch();
+    k_scaled_dipoles<<<vec_grid(3 * L.N, S), 256, 0, st>>>(L, S, x, coef, u64, u32);
+}
+
+}  // namespace eels

@@ -1,0 +1,78 @@
+// Internal launch interface between the host engine and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+namespace eels {
+
+// Process-wide count of kernels this library has launched (graph replays
+// add their kernel nodes; launches recorded during a stream capture are not
+// counted until the graph runs).
+extern std::atomic<long long> g_kernel_launches;
+extern thread_local bool g_capturing;
+inline void count_launch(int n = 1) {
+    if (!g_capturing) g_kernel_launches += n;
+}
+
+// Lattice description shared by every kernel (device pointers).
+struct LatticeDev {
+    int Nx, Ny, Nz, N;            // box extents, occupied cells
+    int Mx, My, Mz;               // padded FFT extents (even)
+    int Hx, Hy, Hz;               // reduced D-hat extents: M/2 + 1
+    const int* cellmap;           // [Nz][Ny][Nx] -> dipole index or -1
+    const uint8_t* mat;           // [N] 0-based material
+    const int* dip_cell;          // [N] linear cell index ix + Nx (iy + Ny iz)
+    const int2* col_range;        // [Ny][Nx] occupied iz range [first, last+1) (first = last = 0 if empty)
+    FftPlan px, py, pz;
+    const double2* tw64x; const double2* tw64y; const double2* tw64z;   // exp(-2 pi i t / M)
+    const float2* tw32x; const float2* tw32y; const float2* tw32z;
+};
+
+// y = diag[m] x - coef[m] * conv(coef[m'] x) / M for a batch of systems.
+// conv(u)_i = sum_{j != i} G~'(r_i - r_j) u_j evaluated by zero-padded FFT.
+// Per-system per-material coefficients are FP64 [S][EELS_MAX_MAT].
+template <typename Rl>
+struct MatvecArgs {
+    const cx<Rl>* x;              // [S][3][N]
+    cx<Rl>* y;                    // [S][3][N]
+    cx<Rl>* U;                    // scratch [S][3][My][Nx][Mz]
+    const cx<Rl>* Dr;             // reduced D-hat [slot][6][Hy][Hx][Hz]
+    const int* sys_slot;          // [S] D-hat slot of each system
+    const double2* coef;          // [S][EELS_MAX_MAT]
+    const double2* diag;          // [S][EELS_MAX_MAT]
+    const int* active;            // [S] or nullptr
+    int S;
+};
+
+template <typename Rl>
+void launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st);
+
+// D-hat build for n_slot energies: kappa[slot] = k d (complex).  G scratch
+// [n_slot][6][My][Mx][Mz] FP64; outputs reduced D-hat FP64 and FP32.
+void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, double2* Gscratch,
+                       double2* Dr64, float2* Dr32, cudaStream_t st);
+
+size_t matvec_smem_bytes(const LatticeDev& L, bool fp64);
+
+// Raise the dynamic shared-memory limit of every kernel instance (call once
+// per device before any launch or stream capture).
+void prepare_kernels();
+
+// Incident field for S systems (per-system params in SysField), FP64 out [S][3][N].
+struct SysField {
+    double2 kt;         // omega d / (gamma_h v): Bessel argument per unit b/d
+    double2 inv_gamma;  // 1 / gamma_h
+    double2 pref_unit;  // phase of the Eq. 25 prefactor
+    double wdv;         // omega d / v
+    double x0, y0;      // beam, lattice units relative to the lattice centre
+};
+void launch_incident_field(const LatticeDev& L, int S, const SysField* sys, double2* e, cudaStream_t st);
+void launch_aux_field(const LatticeDev& L, int S, const SysField* sys, const double2* e, double2* ea, cudaStream_t st);
+void launch_bessel(const double2* z, double2* k0, double2* k1, int n, cudaStream_t st);
+
+}  // namespace eels

@@ -1,0 +1,280 @@
+"""Python binding of libeelsdda (ctypes).  Argument marshalling only: every
+step of the computation runs in the CUDA library.  Function names follow
+the C ABI in include/eelsdda.h.
+
+Importing this module loads the in-tree shared library and raises if it is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libeelsdda.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libeelsdda.so not built ({_LIB_PATH}); run __graft_entry__.build() or "
+                      "python -m paper_2208_01348_gb300.build")
+_lib = C.CDLL(_LIB_PATH)
+
+EELS_OK = 0
+EELS_E_INVALID_ARG = -1
+EELS_E_BEAM_INSIDE = -2
+EELS_E_THRESHOLD = -3
+EELS_E_NOT_CONVERGED = -4
+EELS_E_OOM = -5
+EELS_E_CUDA = -6
+EELS_E_TIMEOUT = -7
+EELS_E_NO_GRID = -8
+EELS_E_UNSUPPORTED = -9
+EELS_FP64 = 0
+EELS_MIXED = 1
+EELS_QMR = 0
+EELS_BICGSTAB = 1
+
+
+class eels_c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class eels_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("d_nm", C.c_double),
+                ("occ", C.POINTER(C.c_uint8))]
+
+
+class eels_beam(C.Structure):
+    _fields_ = [("x0_nm", C.c_double), ("y0_nm", C.c_double)]
+
+
+class eels_opts(C.Structure):
+    _fields_ = [("ekin_keV", C.c_double), ("precision", C.c_int), ("solver", C.c_int),
+                ("eps_it", C.c_double), ("eps_inner", C.c_double), ("max_iter", C.c_int),
+                ("n_dir", C.c_int), ("max_batch", C.c_int)]
+
+
+class eels_point_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("residual", C.c_double), ("converged", C.c_int)]
+
+
+_P = C.c_void_p
+_dp = C.POINTER(C.c_double)
+_cp = C.POINTER(eels_c128)
+_sig = {
+    "eels_default_opts": (None, [C.POINTER(eels_opts)]),
+    "eels_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "eels_destroy": (None, [_P]),
+    "eels_last_error": (C.c_char_p, [_P]),
+    "eels_set_grid": (C.c_int, [_P, C.POINTER(eels_grid)]),
+    "eels_num_dipoles": (C.c_int, [_P]),
+    "eels_padded_dims": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "eels_solve": (C.c_int, [_P, C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp, C.c_int,
+                             C.POINTER(eels_beam), _dp, _dp, _dp, _dp, _cp, C.POINTER(eels_point_stats)]),
+    "eels_query_footprint": (C.c_int, [C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, C.POINTER(C.c_size_t)]),
+    "eels_bessel_k01_dev": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "eels_incident_field": (C.c_int, [_P, C.c_double, C.c_double, eels_c128, eels_beam, _cp, _cp]),
+    "eels_apply_matrix": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _cp, eels_c128, C.c_int, _cp, _cp]),
+    "eels_directions": (C.c_int, [C.c_int, _dp, _dp]),
+    "eels_prepare_operator": (C.c_int, [_P, C.c_int, _dp, C.c_int, _cp, _cp]),
+    "eels_matvec_dev": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "eels_kernel_launches": (C.c_longlong, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class EelsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"eelsdda error {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int, ctx=None):
+    if code != EELS_OK:
+        msg = _lib.eels_last_error(ctx).decode() if ctx else ""
+        raise EelsError(code, msg)
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _cptr(a: np.ndarray):
+    return a.ctypes.data_as(_cp)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def eels_default_opts(**kw) -> eels_opts:
+    o = eels_opts()
+    _lib.eels_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def eels_create(device: int = 0, stream: int = 0):
+    h = _P()
+    _check(_lib.eels_create(C.byref(h), device, _P(stream) if stream else None))
+    return h
+
+
+def eels_destroy(ctx) -> None:
+    _lib.eels_destroy(ctx)
+
+
+def eels_last_error(ctx) -> str:
+    return _lib.eels_last_error(ctx).decode()
+
+
+def _grid(occ: np.ndarray, d_nm: float):
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    nz, ny, nx = occ.shape
+    g = eels_grid(nx, ny, nz, float(d_nm), occ.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return g, occ
+
+
+def eels_set_grid(ctx, occ: np.ndarray, d_nm: float) -> None:
+    g, keep = _grid(occ, d_nm)
+    _check(_lib.eels_set_grid(ctx, C.byref(g)), ctx)
+
+
+def eels_num_dipoles(ctx) -> int:
+    return _lib.eels_num_dipoles(ctx)
+
+
+def eels_padded_dims(ctx):
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.eels_padded_dims(ctx, C.byref(a), C.byref(b), C.byref(c)), ctx)
+    return a.value, b.value, c.value
+
+
+@dataclass
+class SolveResult:
+    p_eels: np.ndarray
+    p_cl: Optional[np.ndarray]
+    p_ext: Optional[np.ndarray]
+    p_abs: Optional[np.ndarray]
+    p: Optional[np.ndarray]
+    iters: np.ndarray
+    refinements: np.ndarray
+    residual: np.ndarray
+    converged: np.ndarray
+    code: int
+
+
+def eels_solve(ctx, opts: eels_opts, energies_eV, eps_p, eps_h, beams_nm, want_cl=True, want_ext=True,
+               want_abs=True, want_p=False, raise_not_converged=True) -> SolveResult:
+    """energies [E]; eps_p [E][n_mat]; eps_h [E]; beams [B][2] -> arrays [E][B]."""
+    e = np.ascontiguousarray(energies_eV, dtype=np.float64).ravel()
+    ne = len(e)
+    ep = _c128(eps_p).reshape(ne, -1)
+    eh = _c128(eps_h).ravel()
+    bm = np.ascontiguousarray(beams_nm, dtype=np.float64).reshape(-1, 2)
+    nb = len(bm)
+    beams = (eels_beam * nb)(*[eels_beam(float(x), float(y)) for x, y in bm])
+    out = {k: np.zeros((ne, nb)) for k in ("eels", "cl", "ext", "abs")}
+    n = eels_num_dipoles(ctx)
+    p = np.zeros((ne, nb, n, 3), dtype=np.complex128) if want_p else None
+    st = (eels_point_stats * (ne * nb))()
+    code = _lib.eels_solve(ctx, C.byref(opts), ne, e.ctypes.data_as(_dp), ep.shape[1], _cptr(ep), _cptr(eh), nb, beams,
+                           _dptr(out["eels"]), _dptr(out["cl"]) if want_cl else None,
+                           _dptr(out["ext"]) if want_ext else None, _dptr(out["abs"]) if want_abs else None,
+                           _cptr(p) if want_p else None, st)
+    if code != EELS_OK and not (code == EELS_E_NOT_CONVERGED and not raise_not_converged):
+        _check(code, ctx)
+    sa = np.array([(s.iters, s.refinements, s.residual, s.converged) for s in st]).reshape(ne, nb, 4)
+    return SolveResult(out["eels"], out["cl"] if want_cl else None, out["ext"] if want_ext else None,
+                       out["abs"] if want_abs else None, p, sa[..., 0].astype(int), sa[..., 1].astype(int),
+                       sa[..., 2], sa[..., 3].astype(bool), code)
+
+
+def eels_query_footprint(occ: np.ndarray, d_nm: float, opts: eels_opts, n_systems: int) -> int:
+    g, keep = _grid(occ, d_nm)
+    b = C.c_size_t()
+    _check(_lib.eels_query_footprint(C.byref(g), C.byref(opts), n_systems, C.byref(b)))
+    return b.value
+
+
+def eels_bessel_k01_dev(z_ptr: int, k0_ptr: int, k1_ptr: int, n: int, stream: int = 0) -> None:
+    _check(_lib.eels_bessel_k01_dev(_P(z_ptr), _P(k0_ptr), _P(k1_ptr), n, _P(stream) if stream else None))
+
+
+def eels_incident_field(ctx, ekin_keV: float, energy_eV: float, eps_h: complex, beam_nm):
+    n = eels_num_dipoles(ctx)
+    e = np.zeros((n, 3), dtype=np.complex128)
+    ea = np.zeros((n, 3), dtype=np.complex128)
+    eh = complex(eps_h)
+    _check(_lib.eels_incident_field(ctx, ekin_keV, energy_eV, eels_c128(eh.real, eh.imag),
+                                    eels_beam(float(beam_nm[0]), float(beam_nm[1])), _cptr(e), _cptr(ea)), ctx)
+    return e, ea
+
+
+def eels_apply_matrix(ctx, precision: int, energy_eV: float, eps_p, eps_h: complex, x: np.ndarray) -> np.ndarray:
+    """x [n_vec][N][3] (or [N][3]) -> A x in SI (m^-3 times the units of x)."""
+    x = _c128(x)
+    single = x.ndim == 2
+    if single:
+        x = x[None]
+    y = np.zeros_like(x)
+    ep = _c128(eps_p).ravel()
+    eh = complex(eps_h)
+    _check(_lib.eels_apply_matrix(ctx, precision, energy_eV, len(ep), _cptr(ep), eels_c128(eh.real, eh.imag),
+                                  x.shape[0], _cptr(x), _cptr(y)), ctx)
+    return y[0] if single else y
+
+
+def eels_prepare_operator(ctx, energies_eV, eps_p, eps_h) -> None:
+    e = np.ascontiguousarray(energies_eV, dtype=np.float64).ravel()
+    ep = _c128(eps_p).reshape(len(e), -1)
+    eh = _c128(eps_h).ravel()
+    _check(_lib.eels_prepare_operator(ctx, len(e), e.ctypes.data_as(_dp), ep.shape[1], _cptr(ep), _cptr(eh)), ctx)
+
+
+def eels_matvec_dev(ctx, precision: int, x_ptr: int, y_ptr: int, n_sys: int, stream: int = 0) -> None:
+    _check(_lib.eels_matvec_dev(ctx, precision, _P(x_ptr), _P(y_ptr), n_sys, _P(stream) if stream else None), ctx)
+
+
+def eels_kernel_launches() -> int:
+    return int(_lib.eels_kernel_launches())
+
+
+def eels_directions(n_dir: int = 2562):
+    d = np.zeros((n_dir, 3))
+    w = np.zeros(n_dir)
+    _check(_lib.eels_directions(n_dir, _dptr(d), _dptr(w)))
+    return d, w
+
+
+class Context:
+    """Owns one eels_ctx (RAII convenience over the functions above)."""
+
+    def __init__(self, device: int = 0, stream: int = 0):
+        self.h = eels_create(device, stream)
+
+    def close(self):
+        if self.h:
+            eels_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,86 @@
+"""The C-ABI library loads, exports every symbol include/eelsdda.h declares,
+and its host-only logic behaves (no GPU compute here)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "eelsdda.h")
+LIB = os.path.join(ROOT, "paper_2208_01348_gb300", "libeelsdda.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_01348_gb300 import build
+    build.build()
+    from paper_2208_01348_gb300 import eelsdda
+    return eelsdda
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eels_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("eels_create", "eels_destroy", "eels_set_grid", "eels_solve", "eels_query_footprint",
+              "eels_last_error", "eels_bessel_k01_dev", "eels_incident_field", "eels_apply_matrix"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (eels_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    assert set(lib.EXPORTED) <= exported
+
+
+def test_default_opts(lib):
+    o = lib.eels_default_opts()
+    assert o.precision == lib.EELS_MIXED and o.solver == lib.EELS_QMR
+    assert o.eps_it == 1e-8 and o.eps_inner == 1e-5 and o.n_dir == 2562
+
+
+def test_host_direction_grid_matches_oracle(lib):
+    from oracle.icosphere import icosphere
+    d, w = lib.eels_directions(2562)
+    V, wo = icosphere(4)
+    assert d.shape == (2562, 3)
+    # same construction -> same vertices (up to rounding order)
+    assert np.allclose(d, V, atol=1e-15, rtol=0)
+    assert np.allclose(w, wo, atol=1e-15, rtol=0)
+    with pytest.raises(lib.EelsError):
+        lib.eels_directions(100)
+
+
+def test_footprint_grows_with_systems(lib):
+    from paper_2208_01348_gb300 import inputs as I
+    occ = I.sphere_occupancy(32, 30.0)
+    o = lib.eels_default_opts()
+    a = lib.eels_query_footprint(occ, 30 / 32, o, 1)
+    b = lib.eels_query_footprint(occ, 30 / 32, o, 200)
+    assert 0 < a < b
+    o64 = lib.eels_default_opts(precision=lib.EELS_FP64)
+    assert lib.eels_query_footprint(occ, 30 / 32, o64, 200) > b
+
+
+@pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="checks the no-GPU error path")
+def test_create_without_gpu_fails_loudly(lib):
+    with pytest.raises(lib.EelsError) as e:
+        lib.eels_create(0)
+    assert e.value.code == lib.EELS_E_CUDA
+
+
+def test_package_import_has_no_fallback():
+    # the product path imports only the CUDA binding; it never touches the oracle
+    pkg = os.path.join(ROOT, "paper_2208_01348_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg, f)).read()
+            assert "import oracle" not in src and "from oracle" not in src, f

@@ -1,0 +1,224 @@
+"""GPU parity: every hot-path step through the C ABI against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances: the FP64 path is held to 1e-10 relative on the probabilities
+and on p; the mixed FP32 + FP64-refinement path to 1e-4 relative on
+P_EELS, P_CL (and P_ext, P_abs) and 1e-4 in relative 2-norm on p.
+Single steps: K0/K1 1e-13, fields 1e-12, FP64 matvec 1e-12, FP32 matvec
+2e-5 (relative 2-norm; the FP32 FFT rounding grows like eps32 * log M)."""
+import numpy as np
+import pytest
+
+from oracle import green, run
+from oracle.constants import NM
+from paper_2208_01348_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_01348_gb300 import eelsdda
+    return eelsdda
+
+
+@pytest.fixture(scope="module")
+def ctx(dd):
+    h = dd.eels_create(0)
+    yield h
+    dd.eels_destroy(h)
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ------------------------------------------------------------------ K0, K1
+def test_bessel_k01_device_matches_scipy(dd):
+    import torch
+    from scipy.special import kv
+    mags = np.geomspace(1e-3, 40.0, 41)
+    args = np.linspace(-np.pi / 2, 0.0, 13)
+    z = (mags[:, None] * np.exp(1j * args[None, :])).ravel()
+    z = np.concatenate([z, [2.0, 2.0000001, -2j, 1.999 - 0.01j, 0.013, 3.1 * np.exp(-1.558j)]])
+    zt = torch.from_numpy(z.astype(np.complex128)).cuda()
+    k0 = torch.empty_like(zt)
+    k1 = torch.empty_like(zt)
+    dd.eels_bessel_k01_dev(zt.data_ptr(), k0.data_ptr(), k1.data_ptr(), len(z), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    g0, g1 = k0.cpu().numpy(), k1.cpu().numpy()
+    r0, r1 = kv(0, z), kv(1, z)
+    assert np.max(np.abs(g0 - r0) / np.abs(r0)) < 1e-13
+    assert np.max(np.abs(g1 - r1) / np.abs(r1)) < 1e-13
+
+
+# ------------------------------------------------------------------ fields
+@pytest.mark.parametrize("eps_h,ekin,e_eV,beam", [
+    (1.0, 100.0, 2.4, (15.0, 0.0)), (2.1025, 120.0, 3.7, (17.0, -4.0)), (4.0 + 0.05j, 200.0, 2.2, (13.0, 6.0)),
+    (4.0, 200.0, 1.6, (0.0, 14.0))])
+def test_incident_and_auxiliary_field(dd, ctx, eps_h, ekin, e_eV, beam):
+    w = I.config_small_sphere()
+    g = w.grid
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    E, Ea = dd.eels_incident_field(ctx, ekin, e_eV, eps_h, beam)
+    pt = run.setup(g.nx, g.ny, g.nz, g.d_nm, g.occ, e_eV, [1.0], eps_h, beam, ekin_keV=ekin)
+    assert rel(E, pt.E_inc) < 1e-12
+    assert rel(Ea, pt.E_a) < 1e-12
+
+
+# ------------------------------------------------------------------ matvec
+def _random_grid(dims, seed, frac=0.7, nmat=1):
+    nx, ny, nz = dims
+    rng = np.random.default_rng(seed)
+    occ = (rng.random((nz, ny, nx)) < frac).astype(np.uint8)
+    if nmat > 1:
+        occ *= rng.integers(1, nmat + 1, size=occ.shape).astype(np.uint8)
+    occ.flat[0] = 1
+    return occ
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (3, 4, 5), (7, 3, 2), (5, 9, 6), (12, 12, 12), (13, 6, 17)])
+def test_matvec_equals_dense_oracle(dd, ctx, dims):
+    nx, ny, nz = dims
+    nmat = 2 if nx * ny * nz > 8 else 1
+    occ = _random_grid(dims, seed=nx * 100 + ny * 10 + nz, nmat=nmat)
+    d_nm = 2.0
+    dd.eels_set_grid(ctx, occ, d_nm)
+    eps_p = [I.drude(2.3), 3.0 + 0.4j][:nmat]
+    eps_h = 2.0 + 0.1j
+    pt = run.setup(nx, ny, nz, d_nm, occ, 2.3, eps_p, eps_h, (100.0, 100.0), ekin_keV=100.0)
+    A = green.dense_matrix(pt.r, pt.k, pt.alpha)
+    x = I.random_complex((3, len(pt.r), 3), seed=5)
+    ref = np.stack([(A @ xi.reshape(-1)).reshape(-1, 3) for xi in x])
+    y64 = dd.eels_apply_matrix(ctx, dd.EELS_FP64, 2.3, eps_p, eps_h, x)
+    y32 = dd.eels_apply_matrix(ctx, dd.EELS_MIXED, 2.3, eps_p, eps_h, x)
+    for i in range(3):
+        assert rel(y64[i], ref[i]) < 1e-12
+        assert rel(y32[i], ref[i]) < 2e-5
+
+
+# ------------------------------------------------------------------ solve
+def _solve(dd, ctx, w, precision, energies=None, beams=None, n_dir=2562, want_p=True, eps=1e-10, max_batch=0):
+    g = w.grid
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    ie = np.arange(len(w.energies_eV)) if energies is None else np.asarray(energies)
+    bm = w.beams_nm if beams is None else np.asarray(beams)
+    o = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=precision, eps_it=eps, n_dir=n_dir, max_batch=max_batch)
+    return dd.eels_solve(ctx, o, w.energies_eV[ie], w.eps_p[ie], w.eps_h[ie], bm, want_p=want_p)
+
+
+def _oracle(w, ie, ib, beams=None):
+    bm = w.beams_nm if beams is None else beams
+    g = w.grid
+    return run.solve_point(g.nx, g.ny, g.nz, g.d_nm, g.occ, w.energies_eV[ie], w.eps_p[ie], w.eps_h[ie], bm[ib],
+                           ekin_keV=w.ekin_keV)
+
+
+def _check_point(res, ie, ib, o, tol_p, tol_vec):
+    for key, got in (("P_EELS", res.p_eels), ("P_CL", res.p_cl), ("P_ext", res.p_ext), ("P_abs", res.p_abs)):
+        assert abs(got[ie, ib] - o[key]) <= tol_p * abs(o[key]), (key, got[ie, ib], o[key])
+    if res.p is not None:
+        assert rel(res.p[ie, ib], o["p"]) < tol_vec
+
+
+def test_small_sphere_fp64_matches_lu(dd, ctx):
+    w = I.config_small_sphere()
+    res = _solve(dd, ctx, w, dd.EELS_FP64, eps=1e-12)
+    assert res.converged.all() and res.residual.max() <= 1e-12
+    _check_point(res, 0, 0, _oracle(w, 0, 0), 1e-10, 1e-10)
+
+
+def test_small_sphere_mixed_matches_lu(dd, ctx):
+    w = I.config_small_sphere()
+    res = _solve(dd, ctx, w, dd.EELS_MIXED, eps=1e-8)
+    assert res.converged.all()
+    _check_point(res, 0, 0, _oracle(w, 0, 0), 1e-4, 1e-4)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_reduced_spectrum_glass_host(dd, ctx, prec):
+    """32^3 sphere config on a 12^3 lattice: same particle, host, electron; 5 energies."""
+    w = I.reduced(I.config_spectrum(), 12 / 32, n_energy=5)
+    p = getattr(dd, "EELS_" + prec)
+    res = _solve(dd, ctx, w, p, eps=1e-12 if prec == "FP64" else 1e-8)
+    tol = 1e-10 if prec == "FP64" else 1e-4
+    for ie in (0, 2, 4):
+        _check_point(res, ie, 0, _oracle(w, ie, 0), tol, tol)
+    # below the Cherenkov threshold the particle loss equals extinction (Sec. 2.4)
+    assert np.allclose(res.p_eels, res.p_ext, rtol=1e-9 if prec == "FP64" else 1e-6, atol=0)
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_reduced_cherenkov_absorbing_host(dd, ctx, prec):
+    """100 nm silver sphere in eps_h = 4 + 0.05i at 200 keV (beta_h > 1) on 12^3."""
+    w = I.reduced(I.config_cherenkov(), 12 / 64, n_energy=3)
+    p = getattr(dd, "EELS_" + prec)
+    res = _solve(dd, ctx, w, p, eps=1e-12 if prec == "FP64" else 1e-8)
+    tol = 1e-10 if prec == "FP64" else 1e-4
+    for ie in range(3):
+        o = _oracle(w, ie, 0)
+        _check_point(res, ie, 0, o, tol, tol)
+        assert abs(o["P_EELS"] - o["P_ext"]) > 1e-3 * abs(o["P_ext"])
+
+
+def test_reduced_rod_map_block_of_beams(dd, ctx):
+    """Rod 40x40x120 nm on 4x4x12 cells, 2 energies x 6 beams solved as one batch."""
+    w = I.reduced(I.config_rod_map(), 4 / 24, n_energy=2)
+    beams = I.rod_raster_beams(3, 2, pitch=9.0)
+    res = _solve(dd, ctx, w, dd.EELS_FP64, beams=beams, eps=1e-12)
+    for ie in range(2):
+        for ib in (0, 3, 5):
+            _check_point(res, ie, ib, _oracle(w, ie, ib, beams), 1e-10, 1e-10)
+
+
+def test_batch_composition_does_not_change_results(dd, ctx):
+    """A point solved alone and inside a larger batch gives identical bits."""
+    w = I.reduced(I.config_spectrum(), 10 / 32, n_energy=4)
+    full = _solve(dd, ctx, w, dd.EELS_MIXED, want_p=False, eps=1e-8)
+    alone = _solve(dd, ctx, w, dd.EELS_MIXED, energies=[2], want_p=False, eps=1e-8)
+    split = _solve(dd, ctx, w, dd.EELS_MIXED, want_p=False, eps=1e-8, max_batch=1)
+    assert full.p_eels[2, 0] == alone.p_eels[0, 0]
+    assert full.p_cl[2, 0] == alone.p_cl[0, 0]
+    assert np.array_equal(full.p_eels, split.p_eels)
+
+
+def test_single_dipole_and_ragged_lattice(dd, ctx):
+    occ = np.ones((1, 1, 1), dtype=np.uint8)
+    w = I.Workload("one", I.Grid(1, 1, 1, 4.0, occ), 100.0, np.array([2.2]), I.drude(np.array([2.2]))[:, None],
+                   np.array([2.1025 + 0j]), np.array([[10.0, 0.0]]))
+    res = _solve(dd, ctx, w, dd.EELS_FP64, eps=1e-13)
+    _check_point(res, 0, 0, _oracle(w, 0, 0), 1e-10, 1e-10)
+    occ = _random_grid((5, 7, 3), seed=3)
+    w2 = I.Workload("ragged", I.Grid(5, 7, 3, 1.5, occ), 150.0, np.array([1.9, 3.3]),
+                    I.drude(np.array([1.9, 3.3]), I.DRUDE_AG)[:, None], np.array([1.7 + 0j, 1.7 + 0j]),
+                    np.array([[9.0, 2.0], [-1.0, 8.0]]))
+    res = _solve(dd, ctx, w2, dd.EELS_FP64, eps=1e-12)
+    for ie in range(2):
+        for ib in range(2):
+            _check_point(res, ie, ib, _oracle(w2, ie, ib), 1e-10, 1e-10)
+
+
+def test_invalid_inputs_raise(dd, ctx):
+    w = I.config_small_sphere()
+    g = w.grid
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    o = dd.eels_default_opts(ekin_keV=100.0)
+    with pytest.raises(dd.EelsError) as e:        # beam through the particle
+        dd.eels_solve(ctx, o, [2.4], [[I.drude(2.4)]], [1.0], [[0.3, 0.2]])
+    assert e.value.code == dd.EELS_E_BEAM_INSIDE
+    with pytest.raises(dd.EelsError) as e:        # active host
+        dd.eels_solve(ctx, o, [2.4], [[I.drude(2.4)]], [1.0 - 0.1j], [[15.0, 0.0]])
+    assert e.value.code == dd.EELS_E_INVALID_ARG
+    from oracle.physics import electron_speed
+    from oracle.constants import C_LIGHT
+    m = C_LIGHT / electron_speed(100.0)
+    with pytest.raises(dd.EelsError) as e:        # exactly at the Cherenkov threshold
+        dd.eels_solve(ctx, o, [2.4], [[I.drude(2.4)]], [m * m], [[15.0, 0.0]])
+    assert e.value.code == dd.EELS_E_THRESHOLD
+    with pytest.raises(dd.EelsError) as e:
+        dd.eels_set_grid(ctx, np.zeros((3, 3, 3), np.uint8), 1.0)
+    assert e.value.code == dd.EELS_E_INVALID_ARG
