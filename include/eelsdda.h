@@ -84,6 +84,8 @@ typedef struct {
     int max_iter;            /* Krylov iterations per inner solve (and in total for EELS_FP64) */
     int n_dir;               /* far-field directions: 0 = no CL, else 10*4^L+2 (icosphere level L; 2562 = L4) */
     int max_batch;           /* (energy, beam) systems solved together; 0 = choose from free memory */
+    int inner_max_iter;      /* EELS_MIXED: FP32 iterations per inner solve before the FP64 residual is
+                                recomputed and the inner solve restarts (0 = max_iter) */
 } eels_opts;
 
 typedef struct {
@@ -94,7 +96,7 @@ typedef struct {
 } eels_point_stats;
 
 /* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR, eps_it 1e-8,
- * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0. */
+ * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 0. */
 void eels_default_opts(eels_opts* opts);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t

@@ -199,15 +199,17 @@ struct eels_ctx {
     bool has_grid = false;
     int nx = 0, ny = 0, nz = 0, N = 0;
     double d_nm = 0;
-    std::vector<int> cellmap_h, dip_cell_h;
-    std::vector<uint8_t> mat_h;
+    std::vector<int> cellmap_h;    // ABI layout cell -> ABI dipole index (x-fastest order), -1 empty
+    std::vector<int> dip_cell_h;   // internal dipole -> cell index
+    std::vector<int> abi_of;       // internal dipole -> ABI dipole index
+    std::vector<uint8_t> mat_h;    // internal dipole -> material (0-based)
     int max_mat = 0;
     LatticeDev L{};
     DevBuf cellmap, mat, dip_cell, col_range, tw64[3], tw32[3];
     // workspace
     DevBuf e64, b64, x64, r64, y64, U, u64, u32;
     DevBuf kv[7];                                          // Krylov vectors V0 V1 P0 P1 P2 W X
-    DevBuf part_a, part_b, qmr, active, next_active, counters, outer, res, rnorm;
+    DevBuf part_a, part_b, qmr, active, upd, counters, outer, res, rnorm, eps_sys;
     DevBuf sysf, coef, diag, wabs, wdv, slot, kappa_sys;
     DevBuf G, Dr64, Dr32, kappa_slot;
     DevBuf lpart, lsums, fpart, fsums, dirs, wts;
@@ -251,20 +253,34 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
         throw Fail{EELS_E_INVALID_ARG, "grid: extents and d must be positive and occ non-NULL"};
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const size_t ncell = (size_t)nx * ny * nz;
+    // ABI numbering: occupied cells in x-fastest order (cellmap_h: cell -> ABI index)
     c->cellmap_h.assign(ncell, -1);
-    c->dip_cell_h.clear();
-    c->mat_h.clear();
-    int maxm = 0;
+    int maxm = 0, nabi = 0;
     for (size_t i = 0; i < ncell; ++i) {
         const int m = g->occ[i];
         if (m == 0) continue;
         if (m > EELS_MAX_MAT) throw Fail{EELS_E_INVALID_ARG, "grid: material index > 8"};
-        c->cellmap_h[i] = (int)c->dip_cell_h.size();
-        c->dip_cell_h.push_back((int)i);
-        c->mat_h.push_back((uint8_t)(m - 1));
+        c->cellmap_h[i] = nabi++;
         maxm = std::max(maxm, m);
     }
-    if (c->dip_cell_h.empty()) throw Fail{EELS_E_INVALID_ARG, "grid: no occupied cell"};
+    if (nabi == 0) throw Fail{EELS_E_INVALID_ARG, "grid: no occupied cell"};
+    // internal numbering: slab-major (ix, iy, iz), z fastest, so that every
+    // x-slab's dipoles are contiguous for the FFT slab kernels
+    std::vector<int> cm_dev(ncell, -1);
+    c->abi_of.clear();
+    c->dip_cell_h.clear();
+    c->mat_h.clear();
+    for (int ix = 0; ix < nx; ++ix)
+        for (int iy = 0; iy < ny; ++iy)
+            for (int iz = 0; iz < nz; ++iz) {
+                const size_t cell = (size_t)ix + (size_t)nx * (iy + (size_t)ny * iz);
+                const int a = c->cellmap_h[cell];
+                if (a < 0) continue;
+                cm_dev[((size_t)ix * ny + iy) * nz + iz] = (int)c->abi_of.size();
+                c->abi_of.push_back(a);
+                c->dip_cell_h.push_back((int)cell);
+                c->mat_h.push_back((uint8_t)(g->occ[cell] - 1));
+            }
     const int Mx = good_fft_len(nx), My = good_fft_len(ny), Mz = good_fft_len(nz);
     if (Mx > 256 || My > 256 || Mz > 256)
         throw Fail{EELS_E_UNSUPPORTED, "grid: padded FFT length above 256 (extent above 128 cells)"};
@@ -284,7 +300,7 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     c->d_nm = g->d_nm;
     c->max_mat = maxm;
     CK(cudaSetDevice(c->device));
-    h2d(c->cellmap, c->cellmap_h, c->stream);
+    h2d(c->cellmap, cm_dev, c->stream);
     h2d(c->mat, c->mat_h, c->stream);
     h2d(c->dip_cell, c->dip_cell_h, c->stream);
     h2d(c->col_range, cr, c->stream);
@@ -375,6 +391,12 @@ size_t per_slot_bytes(const LatticeDev& L) {
     return (size_t)6 * L.Hx * L.Hy * L.Hz * (sizeof(double2) + sizeof(float2));
 }
 
+// Iterations allowed per inner solve: an FP32 inner solve may be restarted
+// early (inner_max_iter) so that rounding in FP32 does not let it stagnate.
+int inner_cap(const eels_opts* o, bool fp32) {
+    return (fp32 && o->inner_max_iter > 0) ? std::min(o->max_iter, o->inner_max_iter) : o->max_iter;
+}
+
 struct Batch {
     int S, e0, e1;   // systems, first/last+1 energy
 };
@@ -387,15 +409,17 @@ KrylovArgs<Rl> krylov_args(eels_ctx* c, int S, const eels_opts* o, double eps) {
     k.S = S;
     k.n3 = n3;
     k.nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
+    k.nblk_a = k.nblk;
     k.V[0] = c->kv[0].as<cx<Rl>>(); k.V[1] = c->kv[1].as<cx<Rl>>();
     k.P[0] = c->kv[2].as<cx<Rl>>(); k.P[1] = c->kv[3].as<cx<Rl>>(); k.P[2] = c->kv[4].as<cx<Rl>>();
     k.W = c->kv[5].as<cx<Rl>>(); k.X = c->kv[6].as<cx<Rl>>();
     k.part_a = c->part_a.as<double>(); k.part_b = c->part_b.as<double>();
     k.qmr = c->qmr.as<QmrState>();
-    k.active = c->active.as<int>(); k.next_active = c->next_active.as<int>();
+    k.active = c->active.as<int>(); k.upd = c->upd.as<int>();
     k.n_active = c->counters.as<int>();
     k.eps = eps;
-    k.max_iter = o->max_iter;
+    k.eps_sys = c->eps_sys.as<double>();
+    k.max_iter = inner_cap(o, sizeof(Rl) == 4);
     return k;
 }
 
@@ -421,14 +445,17 @@ template <typename Rl>
 int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
     cudaStream_t st = c->stream;
     KrylovArgs<Rl> k = krylov_args<Rl>(c, S, o, eps);
+    // the three-pass matvec also returns the per-slab partial sums of v^T (A v)
+    const bool fused = matvec_passes(c->L, sizeof(Rl) == 8) == 3;
+    k.nblk_a = fused ? 3 * c->L.Nx : k.nblk;
     launch_qmr_init<Rl>(k, st);
     CK(cudaGetLastError());
     constexpr int CHUNK = 6;   // period of the vector-slot rotation (2 and 3)
     // every pointer and scalar baked into the captured kernels
     std::vector<const void*> key = {k.V[0], k.V[1], k.P[0], k.P[1], k.P[2], k.W, k.X, c->U.p, dr_of<Rl>(c),
                                     (const void*)(size_t)S, (const void*)(size_t)sizeof(Rl),
-                                    (const void*)(size_t)o->max_iter, c->coef.p, c->diag.p, c->slot.p, c->qmr.p,
-                                    c->part_a.p, c->part_b.p, c->active.p, c->next_active.p, c->counters.p,
+                                    (const void*)(size_t)inner_cap(o, sizeof(Rl) == 4), c->coef.p, c->diag.p, c->slot.p, c->qmr.p,
+                                    c->part_a.p, c->part_b.p, c->active.p, c->upd.p, c->counters.p, c->eps_sys.p,
                                     c->cellmap.p};
     // eps is read inside k_qmr_step from the kernel argument: make it part of the key
     double epsv = eps;
@@ -442,8 +469,9 @@ int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
         g_capturing = true;
         for (int n = 1; n <= CHUNK; ++n) {
             MatvecArgs<Rl> a = mv_args<Rl>(c, S, k.V[n & 1], k.W, dr_of<Rl>(c), k.active, true);
+            a.dot_part = fused ? k.part_a : nullptr;
             launch_matvec<Rl>(c->L, a, st);
-            launch_qmr_post_matvec<Rl>(k, n, st);
+            launch_qmr_post_matvec<Rl>(k, n, fused, st);
         }
         g_capturing = false;
         CK(cudaStreamEndCapture(st, &g));
@@ -462,7 +490,7 @@ int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
         c->graph_key = key;
     }
     int it = 0;
-    const int max_chunks = o->max_iter / CHUNK + 2;
+    const int max_chunks = inner_cap(o, sizeof(Rl) == 4) / CHUNK + 2;
     for (int ch = 0; ch < max_chunks; ++ch) {
         CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -481,13 +509,18 @@ void refine_batch(eels_ctx* c, int S, const eels_opts* o, std::vector<int>& iter
     const int n3 = 3 * c->N;
     const int nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
     int* n_outer = c->counters.as<int>() + 1;
-    const double eps_inner = (sizeof(Rl) == 4) ? std::max(o->eps_inner, 1e-7) : std::max(o->eps_it * 0.5, 1e-15);
-    const int max_outer = (sizeof(Rl) == 4) ? 40 : 6;
+    // inner tolerance per system: an FP32 solve is asked for eps_inner (or
+    // what the next round still needs, if that is less demanding); an FP64
+    // solve is asked for 0.5 eps_it / res, the reduction that reaches eps_it
+    const double eps_floor = (sizeof(Rl) == 4) ? std::max(o->eps_inner, 1e-7) : 1e-15;
+    const double safety = (sizeof(Rl) == 4) ? 0.3 : 0.5;
+    const double eps_inner = eps_floor;
+    const int max_outer = (sizeof(Rl) == 4) ? 200 : 8;
     std::vector<QmrState> qh(S);
     for (int outer_it = 0; outer_it <= max_outer; ++outer_it) {
         launch_norms2(S, n3, nblk, c->r64.as<double2>(), c->b64.as<double2>(), c->part_a.as<double>(), st);
-        launch_residual_check(S, nblk, c->part_a.as<double>(), o->eps_it, c->res.as<double>(), c->rnorm.as<double>(),
-                              c->outer.as<int>(), n_outer, st);
+        launch_residual_check(S, nblk, c->part_a.as<double>(), o->eps_it, eps_floor, safety, c->res.as<double>(),
+                              c->rnorm.as<double>(), c->outer.as<int>(), n_outer, c->eps_sys.as<double>(), st);
         CK(cudaMemcpyAsync(c->pinned, n_outer, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (*c->pinned == 0 || outer_it == max_outer) break;
@@ -573,12 +606,12 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         c->u32.ensure((size_t)S * n3 * sizeof(float2));
         c->U.ensure((size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(double2));
         for (auto& b : c->kv) b.ensure(kvec);
-        c->part_a.ensure((size_t)S * nblk * 4 * sizeof(double));
+        c->part_a.ensure((size_t)S * std::max(nblk, 3 * L.Nx) * 4 * sizeof(double));
         c->part_b.ensure((size_t)S * nblk * 4 * sizeof(double));
         c->qmr.ensure((size_t)S * sizeof(QmrState));
-        c->active.ensure(S * sizeof(int)); c->next_active.ensure(S * sizeof(int)); c->outer.ensure(S * sizeof(int));
+        c->active.ensure(S * sizeof(int)); c->upd.ensure(S * sizeof(int)); c->outer.ensure(S * sizeof(int));
         c->counters.ensure(64);
-        c->res.ensure(S * sizeof(double)); c->rnorm.ensure(S * sizeof(double));
+        c->res.ensure(S * sizeof(double)); c->rnorm.ensure(S * sizeof(double)); c->eps_sys.ensure(S * sizeof(double));
         c->Dr64.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(double2));
         c->Dr32.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(float2));
         // D-hat for the batch energies, in chunks that fit ~1/8 of the system budget
@@ -677,7 +710,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
                     for (int a = 0; a < 3; ++a) {
                         const double2 u = uh[(size_t)s * n3 + (size_t)a * c->N + i];
                         const cd v = fac * cd(u.x, u.y);
-                        p_out[((size_t)g * c->N + i) * 3 + a] = {v.real(), v.imag()};
+                        p_out[((size_t)g * c->N + c->abi_of[i]) * 3 + a] = {v.real(), v.imag()};
                     }
             }
             const bool conv = rs_b[s] <= o->eps_it;
@@ -723,6 +756,7 @@ void eels_default_opts(eels_opts* o) {
     o->max_iter = 20000;
     o->n_dir = 2562;
     o->max_batch = 0;
+    o->inner_max_iter = 0;
 }
 
 int eels_create(eels_ctx** out, int device, void* cuda_stream) {
@@ -768,8 +802,8 @@ void eels_destroy(eels_ctx* c) {
     cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     DevBuf* all[] = {&c->cellmap, &c->mat, &c->dip_cell, &c->col_range, &c->e64, &c->b64, &c->x64, &c->r64, &c->y64,
-                     &c->U, &c->u64, &c->u32, &c->part_a, &c->part_b, &c->qmr, &c->active, &c->next_active,
-                     &c->counters, &c->outer, &c->res, &c->rnorm, &c->sysf, &c->coef, &c->diag, &c->wabs, &c->wdv,
+                     &c->U, &c->u64, &c->u32, &c->part_a, &c->part_b, &c->qmr, &c->active, &c->upd,
+                     &c->counters, &c->outer, &c->res, &c->rnorm, &c->eps_sys, &c->sysf, &c->coef, &c->diag, &c->wabs, &c->wdv,
                      &c->slot, &c->kappa_sys, &c->G, &c->Dr64, &c->Dr32, &c->kappa_slot, &c->lpart, &c->lsums,
                      &c->fpart, &c->fsums, &c->dirs, &c->wts};
     for (DevBuf* b : all) b->release();
@@ -859,8 +893,8 @@ int eels_incident_field(eels_ctx* c, double ekin_keV, double energy_eV, eels_c12
         for (int i = 0; i < c->N; ++i)
             for (int a = 0; a < 3; ++a) {
                 const double2 v = h[(size_t)a * c->N + i], va = ha[(size_t)a * c->N + i];
-                if (e_inc) e_inc[(size_t)i * 3 + a] = {v.x * p.scale, v.y * p.scale};
-                if (e_aux) e_aux[(size_t)i * 3 + a] = {va.x * p.scale, va.y * p.scale};
+                if (e_inc) e_inc[(size_t)c->abi_of[i] * 3 + a] = {v.x * p.scale, v.y * p.scale};
+                if (e_aux) e_aux[(size_t)c->abi_of[i] * 3 + a] = {va.x * p.scale, va.y * p.scale};
             }
         return EELS_OK;
     });
@@ -895,7 +929,7 @@ int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, c
         for (int s = 0; s < S; ++s)
             for (int i = 0; i < c->N; ++i)
                 for (int a = 0; a < 3; ++a) {
-                    const eels_c128 v = x[((size_t)s * c->N + i) * 3 + a];
+                    const eels_c128 v = x[((size_t)s * c->N + c->abi_of[i]) * 3 + a];
                     xh[(size_t)s * n3 + (size_t)a * c->N + i] = make_double2(v.re, v.im);
                 }
         c->x64.ensure(xh.size() * sizeof(double2));
@@ -925,7 +959,7 @@ int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, c
             for (int i = 0; i < c->N; ++i)
                 for (int a = 0; a < 3; ++a) {
                     const double2 v = yh[(size_t)s * n3 + (size_t)a * c->N + i];
-                    y[((size_t)s * c->N + i) * 3 + a] = {v.x * inv_d3, v.y * inv_d3};
+                    y[((size_t)s * c->N + c->abi_of[i]) * 3 + a] = {v.x * inv_d3, v.y * inv_d3};
                 }
         return EELS_OK;
     });

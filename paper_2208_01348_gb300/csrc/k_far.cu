@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(LatticeDev L, const cx<Rl>*
             const int iz = t % Nz, c = (t / Nz) % 3, cc = t / (3 * Nz), colid = c0 + cc;
             C v = mk<C>(0.0, 0.0);
             if (colid < ncol) {
-                const int dip = L.cellmap[(size_t)iz * ncol + colid];
+                const int dip = L.cellmap[((size_t)(colid % L.Nx) * L.Ny + colid / L.Nx) * L.Nz + iz];
                 if (dip >= 0) v = us[(size_t)c * N + dip];
             }
             col[(cc * 3 + c) * Nz + iz] = v;

@@ -15,6 +15,7 @@
 // D-hat is stored on the octant 0 <= k <= M/2 only (6 (M/2+1)^3 values):
 // the diagonal components are even in each k and xy, xz, yz are odd in the
 // two axes they name, so D(M - k) = +-D(k).
+#include <algorithm>
 #include <cstdio>
 
 #include "kernels.h"
@@ -32,15 +33,15 @@ template <> __device__ __forceinline__ const float2* tw_of<float>(const LatticeD
 }
 
 // ---------------------------------------------------------------------------
-// Pass 1: scatter the dipole vector onto the lattice (times coef) and
-// transform along z.  Block: W x-adjacent lines at fixed (s, c, iy).
+// Pass 1 (five-pass path): scatter the dipole vector onto the lattice (times
+// coef) and transform along z.  Block: W y-adjacent lines at fixed (s, c, ix).
 // ---------------------------------------------------------------------------
 template <typename Rl, int W>
 __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(LatticeDev L, MatvecArgs<Rl> a) {
     using C = cx<Rl>;
     const int b = blockIdx.z, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
-    const int iy = blockIdx.y, ix0 = blockIdx.x * W;
+    const int ix = blockIdx.y, iy0 = blockIdx.x * W;
     const int Mz = L.Mz, ls = Mz + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -51,32 +52,34 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(LatticeDev L, MatvecArgs<R
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
     for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
-        const int w = t % W, iz = t / W, ix = ix0 + w;
+        const int iz = t % Mz, w = t / Mz, iy = iy0 + w;
         C v = mk<C>(0.0, 0.0);
-        if (iz < L.Nz && ix < L.Nx) {
-            const int dip = L.cellmap[((size_t)iz * L.Ny + iy) * L.Nx + ix];
+        if (iz < L.Nz && iy < L.Ny) {
+            const int dip = L.cellmap[((size_t)ix * L.Ny + iy) * L.Nz + iz];
             if (dip >= 0) v = xs[dip] * cvt<C>(cf[L.mat[dip]]);
         }
         A[w * ls + iz] = v;
     }
     __syncthreads();
     const C* r = fft_lines<false, false>(A, B, W, ls, 1, L.pz, tw);
-    C* U = a.U + (((size_t)s * 3 + c) * L.My + iy) * (size_t)L.Nx * Mz;
+    C* U = a.U + (((size_t)s * 3 + c) * L.My * L.Nx + ix) * (size_t)Mz;
+    const size_t row = (size_t)L.Nx * Mz;
     for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
-        const int kz = t % Mz, w = t / Mz, ix = ix0 + w;
-        if (ix < L.Nx) U[(size_t)ix * Mz + kz] = r[w * ls + kz];
+        const int kz = t % Mz, w = t / Mz, iy = iy0 + w;
+        if (iy < L.Ny) U[(size_t)iy * row + kz] = r[w * ls + kz];
     }
 }
 
 // ---------------------------------------------------------------------------
-// Pass 5: inverse z transform and gather:  y = diag x - coef conv / M.
+// Pass 5 (five-pass path): inverse z transform and gather:
+//   y = diag x - coef conv / M.
 // ---------------------------------------------------------------------------
 template <typename Rl, int W>
 __global__ void __launch_bounds__(FFT_THREADS) k_zinv(LatticeDev L, MatvecArgs<Rl> a, Rl invM) {
     using C = cx<Rl>;
     const int b = blockIdx.z, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
-    const int iy = blockIdx.y, ix0 = blockIdx.x * W;
+    const int ix = blockIdx.y, iy0 = blockIdx.x * W;
     const int Mz = L.Mz, ls = Mz + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tw = reinterpret_cast<C*>(smem_raw);
@@ -84,10 +87,11 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zinv(LatticeDev L, MatvecArgs<R
     C* B = A + W * ls;
     const C* twg = tw_of<Rl>(L, 2);
     for (int t = threadIdx.x; t < Mz; t += blockDim.x) tw[t] = twg[t];
-    const C* U = a.U + (((size_t)s * 3 + c) * L.My + iy) * (size_t)L.Nx * Mz;
+    const C* U = a.U + (((size_t)s * 3 + c) * L.My * L.Nx + ix) * (size_t)Mz;
+    const size_t row = (size_t)L.Nx * Mz;
     for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
-        const int kz = t % Mz, w = t / Mz, ix = ix0 + w;
-        A[w * ls + kz] = ix < L.Nx ? U[(size_t)ix * Mz + kz] : mk<C>(0.0, 0.0);
+        const int kz = t % Mz, w = t / Mz, iy = iy0 + w;
+        A[w * ls + kz] = iy < L.Ny ? U[(size_t)iy * row + kz] : mk<C>(0.0, 0.0);
     }
     __syncthreads();
     const C* r = fft_lines<true, false>(A, B, W, ls, 1, L.pz, tw);
@@ -96,9 +100,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zinv(LatticeDev L, MatvecArgs<R
     const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
     const double2* dg = a.diag + (size_t)s * EELS_MAX_MAT;
     for (int t = threadIdx.x; t < W * L.Nz; t += blockDim.x) {
-        const int w = t % W, iz = t / W, ix = ix0 + w;
-        if (ix >= L.Nx) continue;
-        const int dip = L.cellmap[((size_t)iz * L.Ny + iy) * L.Nx + ix];
+        const int iz = t % L.Nz, w = t / L.Nz, iy = iy0 + w;
+        if (iy >= L.Ny) continue;
+        const int dip = L.cellmap[((size_t)ix * L.Ny + iy) * L.Nz + iz];
         if (dip < 0) continue;
         const int m = L.mat[dip];
         const C conv = invM * r[w * ls + iz];
@@ -283,6 +287,151 @@ __global__ void k_extract(LatticeDev L, int n_slot, const double2* G, double2* D
 }
 
 // ---------------------------------------------------------------------------
+// Fused slab passes (used when a slab fits shared memory): one block owns
+// the x-slab ix of one (system, component).  Forward: gather the Ny x Nz
+// corner, transform the Nz columns along y (CW at a time, into the slab
+// buffer S[My][Nz]), then the My rows along z (CW at a time) and write the
+// rows of U contiguously.  Inverse: the reverse order, then combine with x
+// and scatter.  Dipoles are numbered slab-major (ix, iy, iz with iz
+// fastest), so each slab's dipoles are contiguous and every global access
+// is coalesced.  This turns the five passes into three.
+// ---------------------------------------------------------------------------
+template <typename Rl, int CW>
+__device__ __forceinline__ void slab_smem(unsigned char* raw, const LatticeDev& L, cx<Rl>*& twy, cx<Rl>*& twz,
+                                          cx<Rl>*& S, cx<Rl>*& A, cx<Rl>*& B) {
+    using C = cx<Rl>;
+    const int scr = max(L.My * (CW + 1), CW * (L.Mz + 1));
+    twy = reinterpret_cast<C*>(raw);
+    twz = twy + L.My;
+    S = twz + L.Mz;
+    A = S + L.My * (L.Nz + 1);
+    B = A + scr;
+    const C* gy = tw_of<Rl>(L, 1);
+    const C* gz = tw_of<Rl>(L, 2);
+    for (int t = threadIdx.x; t < L.My; t += blockDim.x) twy[t] = gy[t];
+    for (int t = threadIdx.x; t < L.Mz; t += blockDim.x) twz[t] = gz[t];
+}
+
+template <typename Rl, int CW>
+__global__ void __launch_bounds__(FFT_THREADS) k_slab_fwd(LatticeDev L, MatvecArgs<Rl> a) {
+    using C = cx<Rl>;
+    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int My = L.My, Mz = L.Mz, Ny = L.Ny, Nz = L.Nz;
+    const int sls = Nz + 1, es = CW + 1, rls = Mz + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *twy, *twz, *S, *A, *B;
+    slab_smem<Rl, CW>(smem_raw, L, twy, twz, S, A, B);
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
+    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    for (int iz0 = 0; iz0 < Nz; iz0 += CW) {
+        for (int t = threadIdx.x; t < My * CW; t += blockDim.x) {
+            const int w = t % CW, y = t / CW, iz = iz0 + w;
+            C v = mk<C>(0.0, 0.0);
+            if (y < Ny && iz < Nz) {
+                const int dip = cm[y * Nz + iz];
+                if (dip >= 0) v = xs[dip] * cvt<C>(cf[L.mat[dip]]);
+            }
+            A[y * es + w] = v;
+        }
+        __syncthreads();
+        const C* r = fft_lines<false, true>(A, B, CW, 1, es, L.py, twy);
+        for (int t = threadIdx.x; t < My * CW; t += blockDim.x) {
+            const int w = t % CW, y = t / CW, iz = iz0 + w;
+            if (iz < Nz) S[y * sls + iz] = r[y * es + w];
+        }
+        __syncthreads();
+    }
+    C* U = a.U + (((size_t)s * 3 + c) * My * L.Nx + ix) * Mz;
+    const size_t row = (size_t)L.Nx * Mz;
+    for (int ky0 = 0; ky0 < My; ky0 += CW) {
+        for (int t = threadIdx.x; t < CW * Mz; t += blockDim.x) {
+            const int z = t % Mz, r = t / Mz, ky = ky0 + r;
+            A[r * rls + z] = (z < Nz && ky < My) ? S[ky * sls + z] : mk<C>(0.0, 0.0);
+        }
+        __syncthreads();
+        const C* rr = fft_lines<false, false>(A, B, CW, rls, 1, L.pz, twz);
+        for (int t = threadIdx.x; t < CW * Mz; t += blockDim.x) {
+            const int z = t % Mz, r = t / Mz, ky = ky0 + r;
+            if (ky < My) U[(size_t)ky * row + z] = rr[r * rls + z];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Rl, int CW>
+__global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecArgs<Rl> a, Rl invM) {
+    using C = cx<Rl>;
+    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int My = L.My, Mz = L.Mz, Ny = L.Ny, Nz = L.Nz;
+    const int sls = Nz + 1, es = CW + 1, rls = Mz + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *twy, *twz, *S, *A, *B;
+    slab_smem<Rl, CW>(smem_raw, L, twy, twz, S, A, B);
+    const C* U = a.U + (((size_t)s * 3 + c) * My * L.Nx + ix) * Mz;
+    const size_t row = (size_t)L.Nx * Mz;
+    for (int ky0 = 0; ky0 < My; ky0 += CW) {
+        for (int t = threadIdx.x; t < CW * Mz; t += blockDim.x) {
+            const int z = t % Mz, r = t / Mz, ky = ky0 + r;
+            A[r * rls + z] = ky < My ? U[(size_t)ky * row + z] : mk<C>(0.0, 0.0);
+        }
+        __syncthreads();
+        const C* rr = fft_lines<true, false>(A, B, CW, rls, 1, L.pz, twz);
+        for (int t = threadIdx.x; t < CW * Nz; t += blockDim.x) {
+            const int z = t % Nz, r = t / Nz, ky = ky0 + r;
+            if (ky < My) S[ky * sls + z] = rr[r * rls + z];
+        }
+        __syncthreads();
+    }
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    C* ys = a.y + ((size_t)s * 3 + c) * L.N;
+    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
+    const double2* dg = a.diag + (size_t)s * EELS_MAX_MAT;
+    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    Rl dot[2] = {0, 0};
+    for (int iz0 = 0; iz0 < Nz; iz0 += CW) {
+        for (int t = threadIdx.x; t < My * CW; t += blockDim.x) {
+            const int w = t % CW, y = t / CW, iz = iz0 + w;
+            A[y * es + w] = iz < Nz ? S[y * sls + iz] : mk<C>(0.0, 0.0);
+        }
+        __syncthreads();
+        const C* r = fft_lines<true, true>(A, B, CW, 1, es, L.py, twy);
+        for (int t = threadIdx.x; t < Ny * CW; t += blockDim.x) {
+            const int w = t % CW, y = t / CW, iz = iz0 + w;
+            if (iz >= Nz) continue;
+            const int dip = cm[y * Nz + iz];
+            if (dip < 0) continue;
+            const int m = L.mat[dip];
+            const C xv = xs[dip];
+            const C yv = cvt<C>(dg[m]) * xv - cvt<C>(cf[m]) * (invM * r[y * es + w]);
+            ys[dip] = yv;
+            dot[0] += xv.x * yv.x - xv.y * yv.y;
+            dot[1] += xv.x * yv.y + xv.y * yv.x;
+        }
+        __syncthreads();
+    }
+    if (a.dot_part) {
+        // block sum in a fixed order (warp shuffles, then thread 0 over the warps)
+        for (int o = 16; o > 0; o >>= 1) {
+            dot[0] += __shfl_xor_sync(0xffffffffu, dot[0], o);
+            dot[1] += __shfl_xor_sync(0xffffffffu, dot[1], o);
+        }
+        Rl* red = reinterpret_cast<Rl*>(A);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) { red[2 * wid] = dot[0]; red[2 * wid + 1] = dot[1]; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0, s1 = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
+            double* p = a.dot_part + (((size_t)s * 3 + c) * L.Nx + ix) * 4;
+            p[0] = s0; p[1] = s1; p[2] = 0.0; p[3] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static const size_t kSmemCap = 220 * 1024;
@@ -334,7 +483,7 @@ template <> const float2* host_tw<float>(const LatticeDev& L, int axis) { return
 
 template <typename Rl, int W>
 static void zpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st) {
-    dim3 grid((L.Nx + W - 1) / W, L.Ny, a.S * 3);
+    dim3 grid((L.Ny + W - 1) / W, L.Nx, a.S * 3);
     const size_t sm = smem_zpass<Rl>(L, W);
     count_launch();
     if (!inv) k_zfwd<Rl, W><<<grid, FFT_THREADS, sm, st>>>(L, a);
@@ -348,8 +497,52 @@ static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStrea
     k_xpass<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
 }
 
+template <typename Rl, int CW> static size_t smem_slab(const LatticeDev& L) {
+    const size_t scr = (size_t)std::max(L.My * (CW + 1), CW * (L.Mz + 1));
+    return ((size_t)L.My + L.Mz + (size_t)L.My * (L.Nz + 1) + 2 * scr) * sizeof(cx<Rl>);
+}
+
+// Widest column tile whose fused-slab shared memory fits one block (0: none).
+template <typename Rl> static int pick_slab(const LatticeDev& L) {
+    if (smem_slab<Rl, 32>(L) <= 110 * 1024) return 32;
+    if (smem_slab<Rl, 16>(L) <= 110 * 1024) return 16;
+    if (smem_slab<Rl, 16>(L) <= kSmemCap) return 16;
+    if (smem_slab<Rl, 8>(L) <= kSmemCap) return 8;
+    return 0;
+}
+
+template <typename Rl, int CW>
+static void slab_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st) {
+    dim3 grid(L.Nx, a.S * 3);
+    const size_t sm = smem_slab<Rl, CW>(L);
+    count_launch();
+    if (!inv) k_slab_fwd<Rl, CW><<<grid, FFT_THREADS, sm, st>>>(L, a);
+    else k_slab_inv<Rl, CW><<<grid, FFT_THREADS, sm, st>>>(L, a, (Rl)(1.0 / ((double)L.Mx * L.My * L.Mz)));
+}
+
+template <typename Rl> static void slab_launch_any(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, int cw,
+                                                   cudaStream_t st) {
+    if (cw == 32) slab_launch<Rl, 32>(L, a, inv, st);
+    else if (cw == 16) slab_launch<Rl, 16>(L, a, inv, st);
+    else slab_launch<Rl, 8>(L, a, inv, st);
+}
+
+template <typename Rl> static void xpass_any(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+    const int wx = pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
+    if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
+    else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
+    else xpass_launch<Rl, 8>(L, a, st);
+}
+
 template <typename Rl>
-void launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+bool launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+    const int cw = pick_slab<Rl>(L);
+    if (cw) {   // three passes: slab (gather, y, z) -> x * D-hat * x -> slab (z, y, scatter)
+        slab_launch_any<Rl>(L, a, false, cw, st);
+        xpass_any<Rl>(L, a, st);
+        slab_launch_any<Rl>(L, a, true, cw, st);
+        return a.dot_part != nullptr;
+    }
     const int wz = pick_w([&](int w) { return smem_zpass<Rl>(L, w); });
     if (wz == 32) zpass_launch<Rl, 32>(L, a, false, st);
     else if (wz == 16) zpass_launch<Rl, 16>(L, a, false, st);
@@ -363,6 +556,7 @@ void launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st
     if (wz == 32) zpass_launch<Rl, 32>(L, a, true, st);
     else if (wz == 16) zpass_launch<Rl, 16>(L, a, true, st);
     else zpass_launch<Rl, 8>(L, a, true, st);
+    return false;
 }
 
 template <typename Rl, int W> static void prepare_w() {
@@ -373,6 +567,8 @@ template <typename Rl, int W> static void prepare_w() {
     allow_smem(k_axis<Rl, W, true, 1>);
     allow_smem(k_axis<Rl, W, false, 2>);
     allow_smem(k_axis<Rl, W, false, 3>);
+    allow_smem(k_slab_fwd<Rl, W>);
+    allow_smem(k_slab_inv<Rl, W>);
 }
 
 void prepare_far_kernels();
@@ -383,8 +579,12 @@ void prepare_kernels() {
     prepare_far_kernels();
 }
 
-template void launch_matvec<float>(const LatticeDev&, const MatvecArgs<float>&, cudaStream_t);
-template void launch_matvec<double>(const LatticeDev&, const MatvecArgs<double>&, cudaStream_t);
+template bool launch_matvec<float>(const LatticeDev&, const MatvecArgs<float>&, cudaStream_t);
+template bool launch_matvec<double>(const LatticeDev&, const MatvecArgs<double>&, cudaStream_t);
+
+int matvec_passes(const LatticeDev& L, bool fp64) {
+    return (fp64 ? pick_slab<double>(L) : pick_slab<float>(L)) ? 3 : 5;
+}
 
 size_t matvec_smem_bytes(const LatticeDev& L, bool fp64) {
     if (fp64) {

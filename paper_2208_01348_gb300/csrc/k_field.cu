@@ -39,7 +39,7 @@ __global__ void k_einc(LatticeDev L, const SysField* sys, double2* e) {
     const size_t N = (size_t)L.N;
     double2* e0 = e + (size_t)s * 3 * N;
     for (int iz = rg.x; iz < rg.y; ++iz) {
-        const int dip = L.cellmap[((size_t)iz * L.Ny + iy) * L.Nx + ix];
+        const int dip = L.cellmap[((size_t)ix * L.Ny + iy) * L.Nz + iz];
         if (dip < 0) continue;
         const double zr = (iz + 0.5) - 0.5 * L.Nz;
         double sn, cs;

@@ -90,7 +90,7 @@ template <typename Rl>
 __global__ void k_qmr_start(KrylovArgs<Rl> k) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k.S) return;
-    if (!k.active[s]) { k.next_active[s] = 0; return; }
+    if (!k.active[s]) return;
     double o[4];
     sum_parts(k.part_a, s, k.nblk, o);     // (b.b, |b|^2)
     QmrState q;
@@ -108,13 +108,13 @@ __global__ void k_qmr_start(KrylovArgs<Rl> k) {
         q.inv_rho = 1.0 / rho;
         q.delta = make_double2(o[0] / (rho * rho), o[1] / (rho * rho));
         q.status = 0;
-        k.next_active[s] = 1;
-    } else {
+    } else {                        // zero right-hand side: x = 0 is exact
         q.inv_rho = 0.0;
         q.delta = make_double2(1, 0);
         q.status = 1;
         q.qres = 0.0;
-        k.next_active[s] = 0;
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
     }
     k.qmr[s] = q;
 }
@@ -143,7 +143,7 @@ __global__ void k_lanczos(KrylovArgs<Rl> k, int n) {
     __shared__ double2 sc[2];
     if (threadIdx.x == 0) {
         double o[4];
-        sum_parts(k.part_a, s, k.nblk, o);
+        sum_parts(k.part_a, s, k.nblk_a, o);
         const QmrState& q = k.qmr[s];
         sc[0] = cdiv(make_double2(o[0], o[1]), q.delta);
         sc[1] = q.beta;
@@ -173,10 +173,10 @@ template <typename Rl>
 __global__ void k_qmr_step(KrylovArgs<Rl> k) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= k.S) return;
-    if (!k.active[s]) { k.next_active[s] = 0; return; }
+    if (!k.active[s]) { k.upd[s] = 0; return; }
     QmrState q = k.qmr[s];
     double oa[4], ob[4];
-    sum_parts(k.part_a, s, k.nblk, oa);
+    sum_parts(k.part_a, s, k.nblk_a, oa);
     sum_parts(k.part_b, s, k.nblk, ob);
     const double2 alpha = cdiv(make_double2(oa[0], oa[1]), q.delta);
     const double rho_n = sqrt(ob[2]);
@@ -214,18 +214,22 @@ __global__ void k_qmr_step(KrylovArgs<Rl> k) {
         q.inv_rho = 0.0;           // invariant subspace reached: the update below is exact
         q.status = 1; next = 0;
     }
-    if (next && q.qres <= k.eps) { q.status = 1; next = 0; }
+    if (next && q.qres <= (k.eps_sys ? k.eps_sys[s] : k.eps)) { q.status = 1; next = 0; }
     if (next && q.iters >= k.max_iter) { q.status = 2; next = 0; }
     if (!(q.qres == q.qres)) { q.status = 3; next = 0; }   // NaN guard
     k.qmr[s] = q;
-    k.next_active[s] = next;
+    k.upd[s] = 1;                   // this iteration's vector update still applies
+    if (!next) {                    // later kernels of the next iterations skip the system
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+    }
 }
 
 // p_n = (v_n - eta p_{n-1} - theta p_{n-2}) / r_n ; x += t p_n ; v_{n+1} = v~ / rho_{n+1}
 template <typename Rl>
 __global__ void k_qmr_update(KrylovArgs<Rl> k, int n) {
     const int s = blockIdx.y;
-    if (!k.active[s]) return;
+    if (!k.upd[s]) return;
     using C = cx<Rl>;
     const QmrState& q = k.qmr[s];
     const C eta = cvt<C>(q.eta), th = cvt<C>(q.theta), ri = cvt<C>(q.rinv), t = cvt<C>(q.t);
@@ -244,14 +248,6 @@ __global__ void k_qmr_update(KrylovArgs<Rl> k, int n) {
     }
 }
 
-__global__ void k_commit(int S, int* active, const int* next_active, int* n_active) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    if (active[s] && !next_active[s]) {
-        active[s] = 0;
-        atomicSub(n_active, 1);
-    }
-}
 
 static inline dim3 vec_grid(int n3, int S) {
     int bx = (n3 + 1023) / 1024;
@@ -267,33 +263,27 @@ void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
     k_qmr_start<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
     count_launch();
     k_qmr_scale<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
-    count_launch();
-    k_commit<<<(k.S + 127) / 128, 128, 0, st>>>(k.S, k.active, k.next_active, k.n_active);
 }
 
 template <typename Rl>
-void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, cudaStream_t st) {
-    count_launch();
-    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.V[n & 1], k.W, k.part_a, k.active);
+void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, bool dot_done, cudaStream_t st) {
+    if (!dot_done) {
+        count_launch();
+        k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.V[n & 1], k.W, k.part_a, k.active);
+    }
     count_launch();
     k_lanczos<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k, n);
     count_launch();
     k_qmr_step<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
     count_launch();
     k_qmr_update<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k, n);
-    count_launch();
-    k_commit<<<(k.S + 127) / 128, 128, 0, st>>>(k.S, k.active, k.next_active, k.n_active);
 }
 
 template void launch_qmr_init<float>(const KrylovArgs<float>&, cudaStream_t);
 template void launch_qmr_init<double>(const KrylovArgs<double>&, cudaStream_t);
-template void launch_qmr_post_matvec<float>(const KrylovArgs<float>&, int, cudaStream_t);
-template void launch_qmr_post_matvec<double>(const KrylovArgs<double>&, int, cudaStream_t);
+template void launch_qmr_post_matvec<float>(const KrylovArgs<float>&, int, bool, cudaStream_t);
+template void launch_qmr_post_matvec<double>(const KrylovArgs<double>&, int, bool, cudaStream_t);
 
-void launch_commit(int S, int* active, const int* next_active, int* n_active, cudaStream_t st) {
-    count_launch();
-    k_commit<<<(S + 127) / 128, 128, 0, st>>>(S, active, next_active, n_active);
-}
 
 // ------------------------------------------------------- FP64 refinement
 __global__ void k_rhs_init(LatticeDev L, int S, const double2* e, const double2* coef, double2* b, double2* x, double2* r) {
@@ -324,8 +314,8 @@ __global__ void k_norms2(int n3, int nblk, const double2* a, const double2* b, d
     }
 }
 
-__global__ void k_residual_check(int S, int nblk, const double* part, double eps, double* res, double* rnorm, int* outer,
-                                 int* n_outer) {
+__global__ void k_residual_check(int S, int nblk, const double* part, double eps, double eps_floor, double safety,
+                                 double* res, double* rnorm, int* outer, int* n_outer, double* eps_sys) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     double o[4];
@@ -336,6 +326,7 @@ __global__ void k_residual_check(int S, int nblk, const double* part, double eps
     rnorm[s] = rn;
     const int go = (r > eps) && (rn > 0.0) && (r == r);
     outer[s] = go;
+    if (eps_sys) eps_sys[s] = go ? fmin(1e-2, fmax(eps_floor, safety * eps / r)) : 1.0;
     if (go) atomicAdd(n_outer, 1);
 }
 
@@ -383,11 +374,12 @@ void launch_norms2(int S, int n3, int nblk, const double2* a, const double2* b, 
     count_launch();
     k_norms2<<<dim3(nblk, S), RED_THREADS, 0, st>>>(n3, nblk, a, b, part);
 }
-void launch_residual_check(int S, int nblk, const double* part, double eps, double* res, double* rnorm, int* outer,
-                           int* n_outer, cudaStream_t st) {
+void launch_residual_check(int S, int nblk, const double* part, double eps, double eps_floor, double safety,
+                           double* res, double* rnorm, int* outer, int* n_outer, double* eps_sys, cudaStream_t st) {
     cudaMemsetAsync(n_outer, 0, sizeof(int), st);
     count_launch();
-    k_residual_check<<<(S + 127) / 128, 128, 0, st>>>(S, nblk, part, eps, res, rnorm, outer, n_outer);
+    k_residual_check<<<(S + 127) / 128, 128, 0, st>>>(S, nblk, part, eps, eps_floor, safety, res, rnorm, outer, n_outer,
+                                                      eps_sys);
 }
 template <typename Rl>
 void launch_make_inner_rhs(int S, int n3, const double2* r, const double* rnorm, const int* outer, cx<Rl>* v,

@@ -24,9 +24,9 @@ struct LatticeDev {
     int Nx, Ny, Nz, N;            // box extents, occupied cells
     int Mx, My, Mz;               // padded FFT extents (even)
     int Hx, Hy, Hz;               // reduced D-hat extents: M/2 + 1
-    const int* cellmap;           // [Nz][Ny][Nx] -> dipole index or -1
+    const int* cellmap;           // [Nx][Ny][Nz] (slab-major) -> internal dipole index or -1
     const uint8_t* mat;           // [N] 0-based material
-    const int* dip_cell;          // [N] linear cell index ix + Nx (iy + Ny iz)
+    const int* dip_cell;          // [N] internal dipole -> cell index ix + Nx (iy + Ny iz)
     const int2* col_range;        // [Ny][Nx] occupied iz range [first, last+1) (first = last = 0 if empty)
     FftPlan px, py, pz;
     const double2* tw64x; const double2* tw64y; const double2* tw64z;   // exp(-2 pi i t / M)
@@ -46,11 +46,14 @@ struct MatvecArgs {
     const double2* coef;          // [S][EELS_MAX_MAT]
     const double2* diag;          // [S][EELS_MAX_MAT]
     const int* active;            // [S] or nullptr
+    double* dot_part;             // optional [S][3 Nx][4]: per-slab sum x.y (unconjugated), written by the
+                                  // three-pass path's last kernel
     int S;
 };
 
+// Returns true when a.dot_part was filled (three-pass path).
 template <typename Rl>
-void launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st);
+bool launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st);
 
 // D-hat build for n_slot energies: kappa[slot] = k d (complex).  G scratch
 // [n_slot][6][My][Mx][Mz] FP64; outputs reduced D-hat FP64 and FP32.
@@ -58,6 +61,7 @@ void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, do
                        double2* Dr64, float2* Dr32, cudaStream_t st);
 
 size_t matvec_smem_bytes(const LatticeDev& L, bool fp64);
+int matvec_passes(const LatticeDev& L, bool fp64);   // 3 (fused slabs) or 5
 
 // Raise the dynamic shared-memory limit of every kernel instance (call once
 // per device before any launch or stream capture).

@@ -31,6 +31,7 @@ struct BicgState {
 template <typename Rl>
 struct KrylovArgs {
     int S, n3, nblk;               // systems, vector length 3N, reduction blocks per system
+    int nblk_a;                    // partial sums of v^T (A v) per system in part_a (3 Nx when the matvec writes them)
     cx<Rl>* V[2];                  // Lanczos vectors (slot n % 2 holds v_n)
     cx<Rl>* P[3];                  // QMR directions (slot n % 3 holds p_n)
     cx<Rl>* W;                     // A v_n, then v~_{n+1}
@@ -42,9 +43,10 @@ struct KrylovArgs {
     QmrState* qmr;
     BicgState* bicg;
     int* active;                   // [S] 1 while the system iterates
-    int* next_active;              // [S]
+    int* upd;                      // [S] 1 if this iteration's vector update applies
     int* n_active;                 // device counter of active systems
     double eps;                    // stop when the (quasi-)residual <= eps ||b||
+    const double* eps_sys;         // per-system eps (overrides eps when non-null)
     int max_iter;
 };
 
@@ -54,13 +56,12 @@ constexpr int RED_CHUNK = 4096;    // vector entries per reduction block
 // QMR (complex symmetric, Freund 1992): start from the rhs stored in V[1].
 template <typename Rl> void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_t st);
 // One QMR iteration n >= 1; the caller supplies the matvec (W = A V[n%2]).
-template <typename Rl> void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, cudaStream_t st);
+template <typename Rl> void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, bool dot_done, cudaStream_t st);
 // BiCGStab (van der Vorst 1992) with the unconjugated shadow residual
 // r^ = r0 (complex-symmetric form); rhs in R, X = 0.
 template <typename Rl> void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st);
 template <typename Rl> void launch_bicg_stage1(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Vb = A Pb
 template <typename Rl> void launch_bicg_stage2(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Tb = A Sb
-void launch_commit(int S, int* active, const int* next_active, int* n_active, cudaStream_t st);
 
 // ---- FP64 refinement helpers (vectors [S][n3]) ----
 // b = coef[mat] * e; x = 0; r = b
@@ -68,9 +69,11 @@ void launch_rhs_init(const LatticeDev& L, int S, const double2* e, const double2
                      double2* r, cudaStream_t st);
 // part[s][blk] = (sum |a|^2, sum |b|^2)
 void launch_norms2(int S, int n3, int nblk, const double2* a, const double2* b, double* part, cudaStream_t st);
-// per system: rn = ||r||, res = rn / ||b||; outer[s] = res > eps; scale[s] = rn
-void launch_residual_check(int S, int nblk, const double* part, double eps, double* res, double* rnorm, int* outer,
-                           int* n_outer, cudaStream_t st);
+// per system: rn = ||r||, res = rn / ||b||; outer[s] = res > eps; rnorm[s] = rn;
+// eps_sys[s] = min(1e-2, max(eps_floor, safety * eps / res)): the relative
+// reduction the next inner solve is asked for (at least 100x per round)
+void launch_residual_check(int S, int nblk, const double* part, double eps, double eps_floor, double safety,
+                           double* res, double* rnorm, int* outer, int* n_outer, double* eps_sys, cudaStream_t st);
 // v32 = r64 / rn (per system) where outer; other systems inactive
 template <typename Rl> void launch_make_inner_rhs(int S, int n3, const double2* r, const double* rnorm, const int* outer,
                                                   cx<Rl>* v, int* active, int* n_active, cudaStream_t st);
