@@ -175,18 +175,141 @@ def run_reference(args, w):
     }))
 
 
+def run_matvec_only(args):
+    """The FFT matvec alone (the dominant kernel set) on S systems of the
+    workload, energies spread over its spectrum; used for ncu captures."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_01348_gb300 import eelsdda as dd
+    w = WORKLOADS[args.workload]()
+    S = args.matvec_only
+    stream = torch.cuda.current_stream()
+    ctx = dd.eels_create(0, stream.cuda_stream)
+    dd.eels_set_grid(ctx, w.grid.occ, w.grid.d_nm)
+    idx = np.linspace(0, len(w.energies_eV) - 1, S).astype(int)
+    dd.eels_prepare_operator(ctx, w.energies_eV[idx], w.eps_p[idx], w.eps_h[idx])
+    n = dd.eels_num_dipoles(ctx)
+    mx, my, mz = dd.eels_padded_dims(ctx)
+    prec = dd.EELS_MIXED if args.precision == "mixed" else dd.EELS_FP64
+    dt = torch.complex64 if prec == dd.EELS_MIXED else torch.complex128
+    x = torch.randn(S, 3, n, dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(4):
+        dd.eels_matvec_dev(ctx, prec, x.data_ptr(), y.data_ptr(), S, stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.matvec_reps):
+        dd.eels_matvec_dev(ctx, prec, x.data_ptr(), y.data_ptr(), S, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.matvec_reps
+    s = 8 if prec == dd.EELS_MIXED else 16
+    M, Mr = mx * my * mz, (mx // 2 + 1) * (my // 2 + 1) * (mz // 2 + 1)
+    alg = S * (6 * M + 6 * Mr + 6 * n) * s
+    peak, kind = measured_peaks()
+    print(json.dumps({"workload": w.name, "systems": S, "precision": args.precision, "ms_per_matvec": ms,
+                      "alg_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak_gbs": peak, "peak_kind": kind,
+                      "frac": alg / (ms * 1e-3) / 1e9 / peak}))
+    dd.eels_destroy(ctx)
+
+
+SERVE_STREAM = dict(rate_per_s=20.0, seed=20261203, n_min=12, n_max=32, beams_max=4, energies_min=4, energies_max=16)
+
+
+
+def run_serve(args):
+    """Serving stream: seeded Poisson arrivals (mean 20/s) of sphere / rod
+    requests (Drude gold or silver, host from {1.0, 2.1, 4.0+0.05i}) admitted
+    by footprint and run concurrently; bounded to args.serve_requests
+    requests with lattices 12-32 cells, 1-4 beams and 4-16 energies so a
+    pass ends within minutes."""
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the serving stream has no CPU reference beyond the per-point oracle"}))
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2208_01348_gb300 import eelsdda as dd
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    reqs = I.serving_stream(n_requests=args.serve_requests, **SERVE_STREAM)
+    warm = I.serving_stream(n_requests=3, **dict(SERVE_STREAM, seed=7))
+
+    def one_pass(stream):
+        srv = dd.eels_server_create(device=local, max_concurrent=args.serve_concurrency)
+        t0 = time.perf_counter()
+        ids = []
+        for r in stream:
+            dt = r.t_arrival_s - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            w = r.workload
+            o = dd.eels_default_opts(ekin_keV=w.ekin_keV, eps_it=1e-8, n_dir=w.n_dir)
+            ids.append((dd.eels_server_submit(srv, w.grid.occ, w.grid.d_nm, o, w.energies_eV, w.eps_p, w.eps_h,
+                                              w.beams_nm), w))
+        lat, pts, t_first, t_last = [], 0, None, 0.0
+        for j, w in ids:
+            code, out, info = dd.eels_server_wait(srv, j, len(w.energies_eV), len(w.beams_nm))
+            assert code in (dd.EELS_OK, dd.EELS_E_NOT_CONVERGED), code
+            lat.append((info["t_end"] - info["t_submit"]) * 1e3)
+            pts += w.n_points
+            t_first = info["t_submit"] if t_first is None else min(t_first, info["t_submit"])
+            t_last = max(t_last, info["t_end"])
+        stats = dd.eels_server_stats(srv)
+        dd.eels_server_destroy(srv)
+        return pts, t_last - t_first, lat, stats
+
+    for _ in range(max(1, args.warmup)):
+        one_pass(warm)
+    l0 = dd.eels_kernel_launches()
+    with ClockSampler(local) as clk:
+        pts, span, lat, stats = one_pass(reqs)
+    launches = dd.eels_kernel_launches() - l0
+    if rank != 0:
+        return
+    value = pts / span
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": span * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic seeded request stream",
+        "config": {"workload": f"serving stream: {len(reqs)} requests, Poisson 20/s, lattices 12-32, "
+                               f"1-4 beams, 4-16 energies, {pts} points", "concurrency": args.serve_concurrency,
+                   "running_max": stats["running_max"]},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(np.max(lat))},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "requests enter and leave through host buffers; the value above is already end to end"},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="spectrum", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="spectrum", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--matvec-only", type=int, default=0,
+                    help="time only the FFT matvec on this many systems of the workload (profiling)")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-concurrency", type=int, default=4)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--matvec-reps", type=int, default=20)
     args = ap.parse_args()
+    if args.workload == "serve":
+        run_serve(args)
+        return
+    if args.matvec_only:
+        run_matvec_only(args)
+        return
     w = WORKLOADS[args.workload]()
     if args.impl == "reference":
         run_reference(args, w)
@@ -300,7 +423,7 @@ def main():
                    "iters_mean": float(np.mean(res.iters)), "residual_max": float(np.max(res.residual))},
         "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-        "roofline": {"bound": "hbm", "kernel": "fft_matvec (5 launches: z, y, x*D*x, y, z passes)",
+        "roofline": {"bound": "hbm", "kernel": "fft_matvec (3 launches: k_slab_fwd, k_xpass, k_slab_inv)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic, "ms_per_matvec": mv_ms, "systems": S,
                      "alg_bytes": alg_bytes},

@@ -96,7 +96,10 @@ typedef struct {
 } eels_point_stats;
 
 /* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR, eps_it 1e-8,
- * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 0. */
+ * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 1000
+ * (FP32 Lanczos recurrences lose biorthogonality on hard systems; restarting
+ * every 1000 iterations from the FP64 residual keeps the iteration count
+ * near that of the FP64 solve). */
 void eels_default_opts(eels_opts* opts);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -182,6 +185,58 @@ int eels_matvec_dev(eels_ctx* ctx, int precision, const void* x, void* y, int n_
 /* Kernels launched by this library in this process so far (graph replays
  * count their kernel nodes). */
 long long eels_kernel_launches(void);
+
+/* ------------------------------------------------------------------------
+ * Serving loop.  Requests (one eels_solve each: a lattice, options and its
+ * (energy, beam) points) are queued in arrival order; a free worker takes the
+ * first waiting request whose device-memory footprint fits the unreserved
+ * budget.  Each worker owns a stream and a context, so admitted requests run
+ * concurrently on the device.  A request's results do not depend on which
+ * other requests run beside it.  The paper runs one independent solver
+ * process per parameter set (Sec. 3.1, Sec. S5); this replaces those runs.
+ * ---------------------------------------------------------------------- */
+typedef struct eels_server eels_server;
+
+enum { EELS_JOB_QUEUED = 0, EELS_JOB_RUNNING = 1, EELS_JOB_DONE = 2, EELS_JOB_FAILED = 3 };
+enum { EELS_SERVER_DRYRUN = 1 };   /* workers hold the slot without GPU work (scheduler tests) */
+
+typedef struct {
+    int device;
+    size_t hbm_budget;       /* bytes admitted requests may reserve (0 = 80% of free memory) */
+    int max_concurrent;      /* worker threads / streams, >= 1 */
+    int flags;               /* EELS_SERVER_DRYRUN or 0 */
+} eels_server_opts;
+
+typedef struct {
+    int state;               /* EELS_JOB_* */
+    int code;                /* eels_solve return code once finished */
+    double t_submit, t_start, t_end;   /* seconds since the server was created */
+    size_t footprint;        /* bytes reserved while running */
+    int n_points;
+} eels_job_info;
+
+int eels_server_create(eels_server** out, const eels_server_opts* opts);
+
+/* Queue a request (all inputs are copied; same meaning as eels_solve).  The
+ * request is batched so that its footprint fits hbm_budget / max_concurrent;
+ * EELS_E_OOM if even one system exceeds hbm_budget. */
+int eels_server_submit(eels_server* s, const eels_grid* grid, const eels_opts* opts, int n_energy,
+                       const double* energy_eV, int n_mat, const eels_c128* eps_p, const eels_c128* eps_h,
+                       int n_beam, const eels_beam* beams, long long* job_id);
+
+/* Non-blocking status of a request. */
+int eels_server_poll(eels_server* s, long long job_id, eels_job_info* info);
+
+/* Block until the request finishes; copy its outputs ([n_energy][n_beam],
+ * any may be NULL) and return its eels_solve code. */
+int eels_server_wait(eels_server* s, long long job_id, double* p_eels, double* p_cl, double* p_ext, double* p_abs,
+                     eels_point_stats* stats, eels_job_info* info);
+
+/* Most requests ever running at once, requests finished, bytes reserved now. */
+int eels_server_stats(eels_server* s, int* running_max, int* completed, size_t* in_use);
+
+/* Finish running requests, drop queued ones, join the workers. */
+void eels_server_destroy(eels_server* s);
 
 /* The far-field direction grid the CL reduction uses (icosphere with
  * n_dir = 10*4^L+2 vertices): dirs [n_dir][3] unit vectors, weights

@@ -63,25 +63,30 @@ struct Fail {
                        std::string(#call) + ": " + cudaGetErrorString(e_)};                          \
     } while (0)
 
+// Device buffer that only grows; allocated stream-ordered on the owning
+// context's stream, so one context's (re)allocation does not synchronise the
+// device under other contexts' work.
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    cudaStream_t* sp = nullptr;   // owning context's stream
     void ensure(size_t n) {
         if (n <= bytes) return;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
+        release();
         if (n == 0) return;
-        cudaError_t e = cudaMalloc(&p, n);
+        cudaError_t e = sp ? cudaMallocAsync(&p, n, *sp) : cudaMalloc(&p, n);
         if (e != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
-            throw Fail{EELS_E_OOM, "cudaMalloc(" + std::to_string(n) + " bytes) failed"};
+            throw Fail{EELS_E_OOM, "device allocation of " + std::to_string(n) + " bytes failed"};
         }
         bytes = n;
     }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (sp) cudaFreeAsync(p, *sp);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
     }
@@ -105,14 +110,30 @@ FftPlan make_plan(int L) {
     p.L = L;
     int r = L;
     std::vector<int> rad;
-    for (int q : {7, 5, 3}) while (r % q == 0) { rad.push_back(q); r /= q; }
+    // power-of-two radices first (largest first: fewer passes over shared
+    // memory, and Ns stays a power of two for shift/mask indexing), then 3, 5, 7
     while (r % 8 == 0) { rad.push_back(8); r /= 8; }
     while (r % 4 == 0) { rad.push_back(4); r /= 4; }
     while (r % 2 == 0) { rad.push_back(2); r /= 2; }
-    // larger radices first reduce the number of passes over shared memory
-    std::sort(rad.begin(), rad.end(), [](int a, int b) { return a > b; });
+    for (int q : {3, 5, 7}) while (r % q == 0) { rad.push_back(q); r /= q; }
+    auto log2_or_neg = [](int v) {
+        if (v <= 0 || (v & (v - 1))) return -1;
+        int s = 0;
+        while ((1 << s) < v) ++s;
+        return s;
+    };
     p.nst = (int)rad.size();
-    for (int i = 0; i < p.nst; ++i) p.radix[i] = rad[i];
+    int Ns = 1;
+    for (int i = 0; i < p.nst; ++i) {
+        FftStage& sd = p.st[i];
+        sd.R = rad[i];
+        sd.Ns = Ns;
+        sd.ns_shift = log2_or_neg(Ns);
+        sd.nb = L / sd.R;
+        sd.nb_shift = log2_or_neg(sd.nb);
+        sd.ts = L / (Ns * sd.R);
+        Ns *= sd.R;
+    }
     return p;
 }
 
@@ -221,6 +242,17 @@ struct eels_ctx {
     long long graph_kernels = 0;
     // operator prepared by eels_prepare_operator
     int op_systems = 0;
+
+    std::vector<DevBuf*> buffers() {
+        std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
+                                  &part_a, &part_b, &qmr, &active, &upd, &counters, &outer, &res, &rnorm, &eps_sys,
+                                  &sysf, &coef, &diag, &wabs, &wdv, &slot, &kappa_sys, &G, &Dr64, &Dr32, &kappa_slot,
+                                  &lpart, &lsums, &fpart, &fsums, &dirs, &wts};
+        for (auto& b : kv) v.push_back(&b);
+        for (auto& b : tw64) v.push_back(&b);
+        for (auto& b : tw32) v.push_back(&b);
+        return v;
+    }
 };
 
 namespace {
@@ -756,7 +788,7 @@ void eels_default_opts(eels_opts* o) {
     o->max_iter = 20000;
     o->n_dir = 2562;
     o->max_batch = 0;
-    o->inner_max_iter = 0;
+    o->inner_max_iter = 1000;
 }
 
 int eels_create(eels_ctx** out, int device, void* cuda_stream) {
@@ -792,6 +824,7 @@ int eels_create(eels_ctx** out, int device, void* cuda_stream) {
         delete c;
         return EELS_E_OOM;
     }
+    for (DevBuf* b : c->buffers()) b->sp = &c->stream;
     *out = c;
     return EELS_OK;
 }
@@ -801,15 +834,8 @@ void eels_destroy(eels_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    DevBuf* all[] = {&c->cellmap, &c->mat, &c->dip_cell, &c->col_range, &c->e64, &c->b64, &c->x64, &c->r64, &c->y64,
-                     &c->U, &c->u64, &c->u32, &c->part_a, &c->part_b, &c->qmr, &c->active, &c->upd,
-                     &c->counters, &c->outer, &c->res, &c->rnorm, &c->eps_sys, &c->sysf, &c->coef, &c->diag, &c->wabs, &c->wdv,
-                     &c->slot, &c->kappa_sys, &c->G, &c->Dr64, &c->Dr32, &c->kappa_slot, &c->lpart, &c->lsums,
-                     &c->fpart, &c->fsums, &c->dirs, &c->wts};
-    for (DevBuf* b : all) b->release();
-    for (auto& b : c->kv) b.release();
-    for (auto& b : c->tw64) b.release();
-    for (auto& b : c->tw32) b.release();
+    for (DevBuf* b : c->buffers()) b->release();
+    cudaStreamSynchronize(c->stream);
     if (c->pinned) cudaFreeHost(c->pinned);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;

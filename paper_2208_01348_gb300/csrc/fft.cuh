@@ -8,7 +8,7 @@
 // b[(j / Ns) Ns R + k + r Ns].  After all stages the result is in natural
 // order.  Forward uses exp(-2 pi i n k / L); the inverse is unnormalised.
 //
-// A "batch of lines" is transformed together: element i of line l lives at
+// A batch of NL lines is transformed together: element i of line l lives at
 // buf[l * lstride + i * estride], so the same routine serves lines stored
 // contiguously (estride = 1) and lines interleaved across a tile
 // (lstride = 1).  Twiddles come from a table tw[t] = exp(-2 pi i t / L).
@@ -20,10 +20,18 @@ namespace eels {
 #define FFT_MAX_STAGES 12
 #define FFT_MAX_LEN 512
 
+// One Stockham stage: radix R after sub-transforms of length Ns; nb = L/R
+// butterflies per line; ts = L/(Ns R) is the twiddle-table stride.  The
+// shifts are log2 of Ns and nb when those are powers of two (else -1), so
+// the index arithmetic of the common power-of-two lengths avoids divisions.
+struct FftStage {
+    int R, Ns, ns_shift, nb, nb_shift, ts;
+};
+
 struct FftPlan {
     int L;
     int nst;
-    int radix[FFT_MAX_STAGES];
+    FftStage st[FFT_MAX_STAGES];
 };
 
 // sqrt(1/2), cos/sin(2 pi/3), and the R = 5, 7 roots of unity (values of
@@ -147,57 +155,163 @@ template <bool INV, typename C> struct Dft<7, INV, C> {
     }
 };
 
-// One Stockham stage of radix R over `nlines` lines.  LINE_FAST: adjacent
+// One Stockham stage of radix R over NL lines.  LINE_FAST: adjacent
 // threads take adjacent lines (good when lstride == 1).
-template <int R, bool INV, bool LINE_FAST, typename C>
-__device__ __forceinline__ void fft_stage(const C* __restrict__ a, C* __restrict__ b, int nlines, int lstride,
-                                          int estride, int L, int Ns, const C* __restrict__ tw) {
-    const int nb = L / R;
-    const int ts = L / (Ns * R);
-    const int total = nlines * nb;
+template <int R, bool INV, bool LINE_FAST, int NL, typename C>
+__device__ __forceinline__ void fft_stage(const C* __restrict__ a, C* __restrict__ b, int lstride, int estride,
+                                          const FftStage sd, const C* __restrict__ tw) {
+    const int nb = sd.nb, Ns = sd.Ns;
+    const int total = NL * nb;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int line, j;
-        if (LINE_FAST) { line = t % nlines; j = t / nlines; }
-        else { j = t % nb; line = t / nb; }
-        const int k = j % Ns;
+        if (LINE_FAST) {
+            line = t % NL;
+            j = t / NL;
+        } else if (sd.nb_shift >= 0) {
+            j = t & (nb - 1);
+            line = t >> sd.nb_shift;
+        } else {
+            j = t % nb;
+            line = t / nb;
+        }
+        int k, jq;
+        if (sd.ns_shift >= 0) {
+            k = j & (Ns - 1);
+            jq = j >> sd.ns_shift;
+        } else {
+            k = j % Ns;
+            jq = j / Ns;
+        }
         const C* src = a + line * lstride;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(j + r * nb) * estride];
         if (Ns > 1) {
+            const int step = k * sd.ts;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = tw[r * k * ts];
+                C w = tw[r * step];
                 if (INV) w.y = -w.y;
                 v[r] = v[r] * w;
             }
         }
         Dft<R, INV, C>::run(v);
         C* dst = b + line * lstride;
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[(base + r * Ns) * estride] = v[r];
     }
 }
 
-// Full transform; returns the buffer that holds the result (a or b).
-// Synchronises the block after every stage (callers sync before the call).
-template <bool INV, bool LINE_FAST, typename C>
-__device__ C* fft_lines(C* a, C* b, int nlines, int lstride, int estride, const FftPlan& p, const C* tw) {
-    int Ns = 1;
+// Stage with arbitrary element access: inputs come from in(line, i), outputs
+// go to out(line, i, value).  Used for the first and last stages, which read
+// and write global memory (or another shared buffer) directly.
+template <int R, bool INV, bool LINE_FAST, int NL, typename C, class In, class Out>
+__device__ __forceinline__ void fft_stage_f(const FftStage sd, const C* __restrict__ tw, In in, Out out) {
+    const int nb = sd.nb, Ns = sd.Ns;
+    const int total = NL * nb;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int line, j;
+        if (LINE_FAST) {
+            line = t % NL;
+            j = t / NL;
+        } else if (sd.nb_shift >= 0) {
+            j = t & (nb - 1);
+            line = t >> sd.nb_shift;
+        } else {
+            j = t % nb;
+            line = t / nb;
+        }
+        int k, jq;
+        if (sd.ns_shift >= 0) {
+            k = j & (Ns - 1);
+            jq = j >> sd.ns_shift;
+        } else {
+            k = j % Ns;
+            jq = j / Ns;
+        }
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in(line, j + r * nb);
+        if (Ns > 1) {
+            const int step = k * sd.ts;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = tw[r * step];
+                if (INV) w.y = -w.y;
+                v[r] = v[r] * w;
+            }
+        }
+        Dft<R, INV, C>::run(v);
+        const int base = jq * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out(line, base + r * Ns, v[r]);
+    }
+}
+
+template <bool INV, bool LINE_FAST, int NL, typename C, class In, class Out>
+__device__ __forceinline__ void fft_stage_any(const FftStage sd, const C* tw, In in, Out out) {
+    switch (sd.R) {
+        case 2: fft_stage_f<2, INV, LINE_FAST, NL>(sd, tw, in, out); break;
+        case 3: fft_stage_f<3, INV, LINE_FAST, NL>(sd, tw, in, out); break;
+        case 4: fft_stage_f<4, INV, LINE_FAST, NL>(sd, tw, in, out); break;
+        case 5: fft_stage_f<5, INV, LINE_FAST, NL>(sd, tw, in, out); break;
+        case 7: fft_stage_f<7, INV, LINE_FAST, NL>(sd, tw, in, out); break;
+        default: fft_stage_f<8, INV, LINE_FAST, NL>(sd, tw, in, out); break;
+    }
+}
+
+// Full transform of NL lines whose inputs are read through ld(line, i) by
+// the first stage and whose outputs are handed to st(line, i, value) by the
+// last stage; the stages in between ping-pong between the shared buffers A
+// and B (element i of line l at l * lstride + i * estride).  The block is
+// synchronised between stages and after the last one.
+template <bool INV, bool LINE_FAST, int NL, typename C, class Ld, class St>
+__device__ void fft_lines_io(C* A, C* B, int lstride, int estride, const FftPlan& p, const C* tw, Ld ld, St st) {
+    auto sm_in = [&](const C* buf) {
+        return [=](int l, int i) { return buf[l * lstride + i * estride]; };
+    };
+    auto sm_out = [&](C* buf) {
+        return [=](int l, int i, C v) { buf[l * lstride + i * estride] = v; };
+    };
+    if (p.nst == 1) {
+        fft_stage_any<INV, LINE_FAST, NL>(p.st[0], tw, ld, st);
+        __syncthreads();
+        return;
+    }
+    fft_stage_any<INV, LINE_FAST, NL>(p.st[0], tw, ld, sm_out(A));
+    __syncthreads();
+    C* a = A;
+    C* b = B;
+    for (int s = 1; s + 1 < p.nst; ++s) {
+        fft_stage_any<INV, LINE_FAST, NL>(p.st[s], tw, sm_in(a), sm_out(b));
+        __syncthreads();
+        C* t = a;
+        a = b;
+        b = t;
+    }
+    fft_stage_any<INV, LINE_FAST, NL>(p.st[p.nst - 1], tw, sm_in(a), st);
+    __syncthreads();
+}
+
+// Full transform of NL lines; returns the buffer that holds the result (a
+// or b).  Synchronises the block after every stage (callers sync before).
+template <bool INV, bool LINE_FAST, int NL, typename C>
+__device__ C* fft_lines(C* a, C* b, int lstride, int estride, const FftPlan& p, const C* tw) {
     for (int st = 0; st < p.nst; ++st) {
-        const int R = p.radix[st];
-        switch (R) {
-            case 2: fft_stage<2, INV, LINE_FAST>(a, b, nlines, lstride, estride, p.L, Ns, tw); break;
-            case 3: fft_stage<3, INV, LINE_FAST>(a, b, nlines, lstride, estride, p.L, Ns, tw); break;
-            case 4: fft_stage<4, INV, LINE_FAST>(a, b, nlines, lstride, estride, p.L, Ns, tw); break;
-            case 5: fft_stage<5, INV, LINE_FAST>(a, b, nlines, lstride, estride, p.L, Ns, tw); break;
-            case 7: fft_stage<7, INV, LINE_FAST>(a, b, nlines, lstride, estride, p.L, Ns, tw); break;
-            default: fft_stage<8, INV, LINE_FAST>(a, b, nlines, lstride, estride, p.L, Ns, tw); break;
+        const FftStage sd = p.st[st];
+        switch (sd.R) {
+            case 2: fft_stage<2, INV, LINE_FAST, NL>(a, b, lstride, estride, sd, tw); break;
+            case 3: fft_stage<3, INV, LINE_FAST, NL>(a, b, lstride, estride, sd, tw); break;
+            case 4: fft_stage<4, INV, LINE_FAST, NL>(a, b, lstride, estride, sd, tw); break;
+            case 5: fft_stage<5, INV, LINE_FAST, NL>(a, b, lstride, estride, sd, tw); break;
+            case 7: fft_stage<7, INV, LINE_FAST, NL>(a, b, lstride, estride, sd, tw); break;
+            default: fft_stage<8, INV, LINE_FAST, NL>(a, b, lstride, estride, sd, tw); break;
         }
         __syncthreads();
-        C* t = a; a = b; b = t;
-        Ns *= R;
+        C* t = a;
+        a = b;
+        b = t;
     }
     return a;
 }

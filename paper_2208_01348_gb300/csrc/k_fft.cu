@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(LatticeDev L, MatvecArgs<R
         A[w * ls + iz] = v;
     }
     __syncthreads();
-    const C* r = fft_lines<false, false>(A, B, W, ls, 1, L.pz, tw);
+    const C* r = fft_lines<false, false, W>(A, B, ls, 1, L.pz, tw);
     C* U = a.U + (((size_t)s * 3 + c) * L.My * L.Nx + ix) * (size_t)Mz;
     const size_t row = (size_t)L.Nx * Mz;
     for (int t = threadIdx.x; t < W * Mz; t += blockDim.x) {
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zinv(LatticeDev L, MatvecArgs<R
         A[w * ls + kz] = iy < L.Ny ? U[(size_t)iy * row + kz] : mk<C>(0.0, 0.0);
     }
     __syncthreads();
-    const C* r = fft_lines<true, false>(A, B, W, ls, 1, L.pz, tw);
+    const C* r = fft_lines<true, false, W>(A, B, ls, 1, L.pz, tw);
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     C* ys = a.y + ((size_t)s * 3 + c) * L.N;
     const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis(cx<Rl>* data, int n1, int 
             A[w * ls + i] = (i < in_len && i2 < n2) ? base[(size_t)i2 * n3 + i] : mk<C>(0.0, 0.0);
         }
         __syncthreads();
-        const C* r = fft_lines<INV, false>(A, B, W, ls, 1, p, tw);
+        const C* r = fft_lines<INV, false, W>(A, B, ls, 1, p, tw);
         for (int t = threadIdx.x; t < W * out_len; t += blockDim.x) {
             const int i = t % out_len, w = t / out_len, i2 = i20 + w;
             if (i2 < n2) base[(size_t)i2 * n3 + i] = r[w * ls + i];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_axis(cx<Rl>* data, int n1, int 
             A[i * es + w] = (i < in_len && i3 < n3) ? d[(size_t)i * stride + i3] : mk<C>(0.0, 0.0);
         }
         __syncthreads();
-        const C* r = fft_lines<INV, true>(A, B, W, 1, es, p, tw);
+        const C* r = fft_lines<INV, true, W>(A, B, 1, es, p, tw);
         for (int t = threadIdx.x; t < W * out_len; t += blockDim.x) {
             const int w = t % W, i = t / W, i3 = i30 + w;
             if (i3 < n3) d[(size_t)i * stride + i3] = r[i * es + w];
@@ -183,17 +183,21 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass(LatticeDev L, MatvecArgs<
     C* B = A + Mx * es;
     const C* twg = tw_of<Rl>(L, 0);
     for (int t = threadIdx.x; t < Mx; t += blockDim.x) tw[t] = twg[t];
+    __syncthreads();
     const size_t plane = (size_t)L.Nx * Mz;
     C* U0 = a.U + ((size_t)s * 3 * L.My + ky) * plane;
     const size_t cstride = (size_t)L.My * plane;
-    for (int t = threadIdx.x; t < NL * Mx; t += blockDim.x) {
-        const int l = t % NL, ix = t / NL, c = l / W, w = l % W, kz = kz0 + w;
-        A[ix * es + l] = (ix < Nx && kz < Mz) ? U0[c * cstride + (size_t)ix * Mz + kz] : mk<C>(0.0, 0.0);
-    }
-    __syncthreads();
-    C* r = fft_lines<false, true>(A, B, NL, 1, es, L.px, tw);
-    C* o = (r == A) ? B : A;
-    // D-hat product
+    const C zero = mk<C>(0.0, 0.0);
+    // forward x transforms of the 3W lines, read straight from U (rows ix >= Nx are zero)
+    C* X = (L.px.nst % 2 == 0) ? B : A;   // the buffer the last forward stage does not read
+    C* Y = (X == A) ? B : A;
+    auto ld = [&](int l, int ix) -> C {
+        const int c = l / W, kz = kz0 + l % W;
+        return (ix < Nx && kz < Mz) ? U0[c * cstride + (size_t)ix * Mz + kz] : zero;
+    };
+    auto stX = [&](int l, int kx, C v) { X[kx * es + l] = v; };
+    fft_lines_io<false, true, NL>(A, B, 1, es, L.px, tw, ld, stX);
+    // D-hat product, in place in X
     const int hx = Mx / 2, hy = L.My / 2, hz = Mz / 2;
     const int kyr = ky <= hy ? ky : L.My - ky;
     const Rl sy = ky <= hy ? (Rl)1 : (Rl)-1;
@@ -209,18 +213,20 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass(LatticeDev L, MatvecArgs<
         const size_t idx = ((size_t)kyr * L.Hx + kxr) * L.Hz + kzr;
         const C dxx = Ds[idx], dxy = (sx * sy) * Ds[cs + idx], dxz = (sx * sz) * Ds[2 * cs + idx];
         const C dyy = Ds[3 * cs + idx], dyz = (sy * sz) * Ds[4 * cs + idx], dzz = Ds[5 * cs + idx];
-        C* e = r + kx * es + w;
-        const C X = e[0], Y = e[W], Z = e[2 * W];
-        e[0] = dxx * X + dxy * Y + dxz * Z;
-        e[W] = dxy * X + dyy * Y + dyz * Z;
-        e[2 * W] = dxz * X + dyz * Y + dzz * Z;
+        C* e = X + kx * es + w;
+        const C Xv = e[0], Yv = e[W], Zv = e[2 * W];
+        e[0] = dxx * Xv + dxy * Yv + dxz * Zv;
+        e[W] = dxy * Xv + dyy * Yv + dyz * Zv;
+        e[2 * W] = dxz * Xv + dyz * Yv + dzz * Zv;
     }
     __syncthreads();
-    const C* r2 = fft_lines<true, true>(r, o, NL, 1, es, L.px, tw);
-    for (int t = threadIdx.x; t < NL * Nx; t += blockDim.x) {
-        const int l = t % NL, ix = t / NL, c = l / W, w = l % W, kz = kz0 + w;
-        if (kz < Mz) U0[c * cstride + (size_t)ix * Mz + kz] = r2[ix * es + l];
-    }
+    // inverse x transforms, the first Nx outputs written straight back to U
+    auto ldX = [&](int l, int kx) -> C { return X[kx * es + l]; };
+    auto st = [&](int l, int ix, C v) {
+        const int c = l / W, kz = kz0 + l % W;
+        if (ix < Nx && kz < Mz) U0[c * cstride + (size_t)ix * Mz + kz] = v;
+    };
+    fft_lines_io<true, true, NL>(Y, X, 1, es, L.px, tw, ldX, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,11 +302,15 @@ __global__ void k_extract(LatticeDev L, int n_slot, const double2* G, double2* D
 // fastest), so each slab's dipoles are contiguous and every global access
 // is coalesced.  This turns the five passes into three.
 // ---------------------------------------------------------------------------
+// Row stride of the z-transform tile: runs of 8 elements of consecutive rows
+// fall in disjoint bank groups when the stride is 8 mod 16.
+__host__ __device__ __forceinline__ int slab_row_stride(int Mz) { return Mz + ((Mz % 16 == 0) ? 8 : 1); }
+
 template <typename Rl, int CW>
 __device__ __forceinline__ void slab_smem(unsigned char* raw, const LatticeDev& L, cx<Rl>*& twy, cx<Rl>*& twz,
                                           cx<Rl>*& S, cx<Rl>*& A, cx<Rl>*& B) {
     using C = cx<Rl>;
-    const int scr = max(L.My * (CW + 1), CW * (L.Mz + 1));
+    const int scr = max(L.My * (CW + 1), CW * slab_row_stride(L.Mz));
     twy = reinterpret_cast<C*>(raw);
     twz = twy + L.My;
     S = twz + L.Mz;
@@ -317,46 +327,43 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_fwd(LatticeDev L, MatvecAr
     using C = cx<Rl>;
     const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
-    const int My = L.My, Mz = L.Mz, Ny = L.Ny, Nz = L.Nz;
-    const int sls = Nz + 1, es = CW + 1, rls = Mz + 1;
+    const int My = L.My, Ny = L.Ny, Nz = L.Nz;
+    const int sls = Nz + 1, es = CW + 1, rls = slab_row_stride(L.Mz);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *twy, *twz, *S, *A, *B;
     slab_smem<Rl, CW>(smem_raw, L, twy, twz, S, A, B);
+    __syncthreads();
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
     const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    const C zero = mk<C>(0.0, 0.0);
+    // y transforms of the Nz columns (CW at a time): gathered from x, into S
     for (int iz0 = 0; iz0 < Nz; iz0 += CW) {
-        for (int t = threadIdx.x; t < My * CW; t += blockDim.x) {
-            const int w = t % CW, y = t / CW, iz = iz0 + w;
-            C v = mk<C>(0.0, 0.0);
-            if (y < Ny && iz < Nz) {
-                const int dip = cm[y * Nz + iz];
-                if (dip >= 0) v = xs[dip] * cvt<C>(cf[L.mat[dip]]);
-            }
-            A[y * es + w] = v;
-        }
-        __syncthreads();
-        const C* r = fft_lines<false, true>(A, B, CW, 1, es, L.py, twy);
-        for (int t = threadIdx.x; t < My * CW; t += blockDim.x) {
-            const int w = t % CW, y = t / CW, iz = iz0 + w;
-            if (iz < Nz) S[y * sls + iz] = r[y * es + w];
-        }
-        __syncthreads();
+        auto ld = [&](int l, int y) -> C {
+            const int iz = iz0 + l;
+            if (y >= Ny || iz >= Nz) return zero;
+            const int dip = cm[y * Nz + iz];
+            return dip >= 0 ? xs[dip] * cvt<C>(cf[L.mat[dip]]) : zero;
+        };
+        auto st = [&](int l, int y, C v) {
+            const int iz = iz0 + l;
+            if (iz < Nz) S[y * sls + iz] = v;
+        };
+        fft_lines_io<false, true, CW>(A, B, 1, es, L.py, twy, ld, st);
     }
-    C* U = a.U + (((size_t)s * 3 + c) * My * L.Nx + ix) * Mz;
-    const size_t row = (size_t)L.Nx * Mz;
+    // z transforms of the My rows (CW at a time): from S, rows written to U
+    C* U = a.U + (((size_t)s * 3 + c) * My * L.Nx + ix) * L.Mz;
+    const size_t row = (size_t)L.Nx * L.Mz;
     for (int ky0 = 0; ky0 < My; ky0 += CW) {
-        for (int t = threadIdx.x; t < CW * Mz; t += blockDim.x) {
-            const int z = t % Mz, r = t / Mz, ky = ky0 + r;
-            A[r * rls + z] = (z < Nz && ky < My) ? S[ky * sls + z] : mk<C>(0.0, 0.0);
-        }
-        __syncthreads();
-        const C* rr = fft_lines<false, false>(A, B, CW, rls, 1, L.pz, twz);
-        for (int t = threadIdx.x; t < CW * Mz; t += blockDim.x) {
-            const int z = t % Mz, r = t / Mz, ky = ky0 + r;
-            if (ky < My) U[(size_t)ky * row + z] = rr[r * rls + z];
-        }
-        __syncthreads();
+        auto ld = [&](int l, int z) -> C {
+            const int ky = ky0 + l;
+            return (z < Nz && ky < My) ? S[ky * sls + z] : zero;
+        };
+        auto st = [&](int l, int z, C v) {
+            const int ky = ky0 + l;
+            if (ky < My) U[(size_t)ky * row + z] = v;
+        };
+        fft_lines_io<false, false, CW>(A, B, rls, 1, L.pz, twz, ld, st);
     }
 }
 
@@ -365,26 +372,28 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
     using C = cx<Rl>;
     const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
-    const int My = L.My, Mz = L.Mz, Ny = L.Ny, Nz = L.Nz;
-    const int sls = Nz + 1, es = CW + 1, rls = Mz + 1;
+    const int My = L.My, Ny = L.Ny, Nz = L.Nz;
+    const int sls = Nz + 1, es = CW + 1, rls = slab_row_stride(L.Mz);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *twy, *twz, *S, *A, *B;
     slab_smem<Rl, CW>(smem_raw, L, twy, twz, S, A, B);
-    const C* U = a.U + (((size_t)s * 3 + c) * My * L.Nx + ix) * Mz;
-    const size_t row = (size_t)L.Nx * Mz;
+    __syncthreads();
+    const C zero = mk<C>(0.0, 0.0);
+    // inverse z transforms of the My rows of U (CW at a time), first Nz outputs into S
+    const C* U = a.U + (((size_t)s * 3 + c) * My * L.Nx + ix) * L.Mz;
+    const size_t row = (size_t)L.Nx * L.Mz;
     for (int ky0 = 0; ky0 < My; ky0 += CW) {
-        for (int t = threadIdx.x; t < CW * Mz; t += blockDim.x) {
-            const int z = t % Mz, r = t / Mz, ky = ky0 + r;
-            A[r * rls + z] = ky < My ? U[(size_t)ky * row + z] : mk<C>(0.0, 0.0);
-        }
-        __syncthreads();
-        const C* rr = fft_lines<true, false>(A, B, CW, rls, 1, L.pz, twz);
-        for (int t = threadIdx.x; t < CW * Nz; t += blockDim.x) {
-            const int z = t % Nz, r = t / Nz, ky = ky0 + r;
-            if (ky < My) S[ky * sls + z] = rr[r * rls + z];
-        }
-        __syncthreads();
+        auto ld = [&](int l, int z) -> C {
+            const int ky = ky0 + l;
+            return ky < My ? U[(size_t)ky * row + z] : zero;
+        };
+        auto st = [&](int l, int z, C v) {
+            const int ky = ky0 + l;
+            if (ky < My && z < Nz) S[ky * sls + z] = v;
+        };
+        fft_lines_io<true, false, CW>(A, B, rls, 1, L.pz, twz, ld, st);
     }
+    // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     C* ys = a.y + ((size_t)s * 3 + c) * L.N;
     const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
@@ -392,25 +401,23 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
     const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
     Rl dot[2] = {0, 0};
     for (int iz0 = 0; iz0 < Nz; iz0 += CW) {
-        for (int t = threadIdx.x; t < My * CW; t += blockDim.x) {
-            const int w = t % CW, y = t / CW, iz = iz0 + w;
-            A[y * es + w] = iz < Nz ? S[y * sls + iz] : mk<C>(0.0, 0.0);
-        }
-        __syncthreads();
-        const C* r = fft_lines<true, true>(A, B, CW, 1, es, L.py, twy);
-        for (int t = threadIdx.x; t < Ny * CW; t += blockDim.x) {
-            const int w = t % CW, y = t / CW, iz = iz0 + w;
-            if (iz >= Nz) continue;
+        auto ld = [&](int l, int y) -> C {
+            const int iz = iz0 + l;
+            return iz < Nz ? S[y * sls + iz] : zero;
+        };
+        auto st = [&](int l, int y, C v) {
+            const int iz = iz0 + l;
+            if (y >= Ny || iz >= Nz) return;
             const int dip = cm[y * Nz + iz];
-            if (dip < 0) continue;
+            if (dip < 0) return;
             const int m = L.mat[dip];
             const C xv = xs[dip];
-            const C yv = cvt<C>(dg[m]) * xv - cvt<C>(cf[m]) * (invM * r[y * es + w]);
+            const C yv = cvt<C>(dg[m]) * xv - cvt<C>(cf[m]) * (invM * v);
             ys[dip] = yv;
             dot[0] += xv.x * yv.x - xv.y * yv.y;
             dot[1] += xv.x * yv.y + xv.y * yv.x;
-        }
-        __syncthreads();
+        };
+        fft_lines_io<true, true, CW>(A, B, 1, es, L.py, twy, ld, st);
     }
     if (a.dot_part) {
         // block sum in a fixed order (warp shuffles, then thread 0 over the warps)
@@ -498,7 +505,7 @@ static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStrea
 }
 
 template <typename Rl, int CW> static size_t smem_slab(const LatticeDev& L) {
-    const size_t scr = (size_t)std::max(L.My * (CW + 1), CW * (L.Mz + 1));
+    const size_t scr = (size_t)std::max(L.My * (CW + 1), CW * slab_row_stride(L.Mz));
     return ((size_t)L.My + L.Mz + (size_t)L.My * (L.Nz + 1) + 2 * scr) * sizeof(cx<Rl>);
 }
 
@@ -527,8 +534,16 @@ template <typename Rl> static void slab_launch_any(const LatticeDev& L, const Ma
     else slab_launch<Rl, 8>(L, a, inv, st);
 }
 
+// The x pass is latency-bound on its global loads: prefer the tile that
+// keeps four blocks resident per SM.
+template <typename Rl> static int pick_xpass_w(const LatticeDev& L) {
+    for (int W : {32, 16})
+        if (smem_xpass<Rl>(L, W) <= 56 * 1024) return W;
+    return pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
+}
+
 template <typename Rl> static void xpass_any(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
-    const int wx = pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
+    const int wx = pick_xpass_w<Rl>(L);
     if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
     else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
     else xpass_launch<Rl, 8>(L, a, st);
@@ -548,10 +563,7 @@ bool launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st
     else if (wz == 16) zpass_launch<Rl, 16>(L, a, false, st);
     else zpass_launch<Rl, 8>(L, a, false, st);
     axis_launch<Rl, false, 1>(a.U, a.S * 3, L.My, L.Nx, L.Mz, L.Ny, L.My, L.py, host_tw<Rl>(L, 1), a.active, 3, st);
-    const int wx = pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
-    if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
-    else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
-    else xpass_launch<Rl, 8>(L, a, st);
+    xpass_any<Rl>(L, a, st);
     axis_launch<Rl, true, 1>(a.U, a.S * 3, L.My, L.Nx, L.Mz, L.My, L.Ny, L.py, host_tw<Rl>(L, 1), a.active, 3, st);
     if (wz == 32) zpass_launch<Rl, 32>(L, a, true, st);
     else if (wz == 16) zpass_launch<Rl, 16>(L, a, true, st);

@@ -59,6 +59,18 @@ class eels_point_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("residual", C.c_double), ("converged", C.c_int)]
 
 
+class eels_server_opts(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget", C.c_size_t), ("max_concurrent", C.c_int), ("flags", C.c_int)]
+
+
+class eels_job_info(C.Structure):
+    _fields_ = [("state", C.c_int), ("code", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_end", C.c_double), ("footprint", C.c_size_t), ("n_points", C.c_int)]
+
+
+EELS_JOB_QUEUED, EELS_JOB_RUNNING, EELS_JOB_DONE, EELS_JOB_FAILED = 0, 1, 2, 3
+EELS_SERVER_DRYRUN = 1
+
 _P = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _cp = C.POINTER(eels_c128)
@@ -80,6 +92,14 @@ _sig = {
     "eels_prepare_operator": (C.c_int, [_P, C.c_int, _dp, C.c_int, _cp, _cp]),
     "eels_matvec_dev": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_kernel_launches": (C.c_longlong, []),
+    "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
+    "eels_server_submit": (C.c_int, [_P, C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp,
+                                     C.c_int, C.POINTER(eels_beam), C.POINTER(C.c_longlong)]),
+    "eels_server_poll": (C.c_int, [_P, C.c_longlong, C.POINTER(eels_job_info)]),
+    "eels_server_wait": (C.c_int, [_P, C.c_longlong, _dp, _dp, _dp, _dp, C.POINTER(eels_point_stats),
+                                   C.POINTER(eels_job_info)]),
+    "eels_server_stats": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)]),
+    "eels_server_destroy": (None, [_P]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -278,3 +298,54 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- serving loop
+def eels_server_create(device: int = 0, hbm_budget: int = 0, max_concurrent: int = 4, flags: int = 0):
+    h = _P()
+    o = eels_server_opts(device, hbm_budget, max_concurrent, flags)
+    _check(_lib.eels_server_create(C.byref(h), C.byref(o)))
+    return h
+
+
+def eels_server_submit(srv, occ: np.ndarray, d_nm: float, opts: eels_opts, energies_eV, eps_p, eps_h, beams_nm) -> int:
+    g, keep = _grid(occ, d_nm)
+    e = np.ascontiguousarray(energies_eV, dtype=np.float64).ravel()
+    ep = _c128(eps_p).reshape(len(e), -1)
+    eh = _c128(eps_h).ravel()
+    bm = np.ascontiguousarray(beams_nm, dtype=np.float64).reshape(-1, 2)
+    beams = (eels_beam * len(bm))(*[eels_beam(float(x), float(y)) for x, y in bm])
+    jid = C.c_longlong()
+    _check(_lib.eels_server_submit(srv, C.byref(g), C.byref(opts), len(e), e.ctypes.data_as(_dp), ep.shape[1],
+                                   _cptr(ep), _cptr(eh), len(bm), beams, C.byref(jid)))
+    return jid.value
+
+
+def _info_dict(i: eels_job_info) -> dict:
+    return dict(state=i.state, code=i.code, t_submit=i.t_submit, t_start=i.t_start, t_end=i.t_end,
+                footprint=i.footprint, n_points=i.n_points)
+
+
+def eels_server_poll(srv, job: int) -> dict:
+    i = eels_job_info()
+    _check(_lib.eels_server_poll(srv, job, C.byref(i)))
+    return _info_dict(i)
+
+
+def eels_server_wait(srv, job: int, n_energy: int, n_beam: int, want_cl: bool = True):
+    out = {k: np.zeros((n_energy, n_beam)) for k in ("eels", "cl", "ext", "abs")}
+    st = (eels_point_stats * (n_energy * n_beam))()
+    i = eels_job_info()
+    code = _lib.eels_server_wait(srv, job, _dptr(out["eels"]), _dptr(out["cl"]) if want_cl else None,
+                                 _dptr(out["ext"]), _dptr(out["abs"]), st, C.byref(i))
+    return code, out, _info_dict(i)
+
+
+def eels_server_stats(srv):
+    a, b, c = C.c_int(), C.c_int(), C.c_size_t()
+    _check(_lib.eels_server_stats(srv, C.byref(a), C.byref(b), C.byref(c)))
+    return dict(running_max=a.value, completed=b.value, in_use=c.value)
+
+
+def eels_server_destroy(srv) -> None:
+    _lib.eels_server_destroy(srv)
