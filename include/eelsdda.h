@@ -187,6 +187,33 @@ int eels_matvec_dev(eels_ctx* ctx, int precision, const void* x, void* y, int n_
 long long eels_kernel_launches(void);
 
 /* ------------------------------------------------------------------------
+ * The same matrix-vector product for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a library-integration
+ * entry point.  Callers that cannot let a library allocate at the time of
+ * the call include code that runs while a stream is being captured into a
+ * CUDA graph (the allocator may not be called there), real-time or
+ * latency-critical loops that must not meet the allocator's implicit
+ * synchronisation, and hosts that own all device memory through their own
+ * pool.  eels_matvec_dev_noalloc applies the operator prepared by
+ * eels_prepare_operator with the same kernels as eels_matvec_dev, but takes
+ * its FFT scratch from one fixed array compiled into the library
+ * (EELS_NOALLOC_SCRATCH_BYTES = 64 MiB of device memory, held by every GPU
+ * that loads the library until the process exits) and calls no allocator.
+ *
+ *  - Arguments as for eels_matvec_dev.  The scratch needed is
+ *    n_sys * 3 * My * Nx * Mz * (8 or 16 bytes); larger requests return
+ *    EELS_E_UNSUPPORTED ("pass fewer systems per call") before any launch.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; nothing in it has to start at zero (each call writes every
+ *    scratch element it reads first).  Calls that overlap on the GPU (two
+ *    streams, two threads, two contexts) race on the array: serialise them. */
+#define EELS_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+int eels_matvec_dev_noalloc(eels_ctx* ctx, int precision, const void* x, void* y, int n_sys, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Serving loop.  Requests (one eels_solve each: a lattice, options and its
  * (energy, beam) points) are queued in arrival order; a free worker takes the
  * first waiting request whose device-memory footprint fits the unreserved

@@ -1050,6 +1050,41 @@ int eels_matvec_dev(eels_ctx* c, int precision, const void* x, void* y, int n_sy
 
 long long eels_kernel_launches(void) { return g_kernel_launches.load(); }
 
+}  // extern "C"
+
+// Launch the prepared operator with caller-provided FFT scratch (used by
+// eels_matvec_dev_noalloc, which owns a fixed array).  Allocates nothing.
+int eels_internal_matvec_with_scratch(eels_ctx* c, int precision, const void* x, void* y, int n_sys, void* stream,
+                                      void* scratch, size_t scratch_bytes) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+        if (n_sys <= 0 || n_sys > c->op_systems || !x || !y)
+            throw Fail{EELS_E_INVALID_ARG, "matvec: n_sys must be in [1, prepared systems]"};
+        const LatticeDev& L = c->L;
+        const size_t elem = precision == EELS_FP64 ? sizeof(double2) : sizeof(float2);
+        const size_t need = (size_t)n_sys * 3 * L.My * L.Nx * L.Mz * elem;
+        if (need > scratch_bytes)
+            throw Fail{EELS_E_UNSUPPORTED, "eels_matvec_dev_noalloc: " + std::to_string(n_sys) + " systems need " +
+                                               std::to_string(need) + " bytes of FFT scratch, more than the fixed " +
+                                               std::to_string(scratch_bytes) + "-byte array; pass fewer systems per call"};
+        cudaStream_t st = (cudaStream_t)stream;
+        if (precision == EELS_FP64) {
+            MatvecArgs<double> a = mv_args<double>(c, n_sys, (const double2*)x, (double2*)y, c->Dr64.as<double2>(), nullptr, true);
+            a.U = reinterpret_cast<double2*>(scratch);
+            launch_matvec<double>(L, a, st);
+        } else {
+            MatvecArgs<float> a = mv_args<float>(c, n_sys, (const float2*)x, (float2*)y, c->Dr32.as<float2>(), nullptr, true);
+            a.U = reinterpret_cast<float2*>(scratch);
+            launch_matvec<float>(L, a, st);
+        }
+        CK(cudaGetLastError());
+        return EELS_OK;
+    });
+}
+
+extern "C" {
+
 int eels_directions(int n_dir, double* dirs, double* weights) {
     std::vector<double> d, w;
     if (!dirs || !weights || !icosphere(n_dir, d, w)) return EELS_E_INVALID_ARG;

@@ -92,6 +92,7 @@ _sig = {
     "eels_prepare_operator": (C.c_int, [_P, C.c_int, _dp, C.c_int, _cp, _cp]),
     "eels_matvec_dev": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_kernel_launches": (C.c_longlong, []),
+    "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
     "eels_server_submit": (C.c_int, [_P, C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp,
                                      C.c_int, C.POINTER(eels_beam), C.POINTER(C.c_longlong)]),
@@ -263,6 +264,18 @@ def eels_prepare_operator(ctx, energies_eV, eps_p, eps_h) -> None:
 
 def eels_matvec_dev(ctx, precision: int, x_ptr: int, y_ptr: int, n_sys: int, stream: int = 0) -> None:
     _check(_lib.eels_matvec_dev(ctx, precision, _P(x_ptr), _P(y_ptr), n_sys, _P(stream) if stream else None), ctx)
+
+
+EELS_NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def eels_matvec_dev_noalloc(ctx, precision: int, x_ptr: int, y_ptr: int, n_sys: int, stream: int = 0) -> None:
+    """eels_matvec_dev without any device allocation: the FFT scratch is a
+    fixed 64 MiB array inside the library, shared by every call on a device
+    (serialise overlapping calls; make the first call on a device before any
+    stream capture)."""
+    _check(_lib.eels_matvec_dev_noalloc(ctx, precision, _P(x_ptr), _P(y_ptr), n_sys, _P(stream) if stream else None),
+           ctx)
 
 
 def eels_kernel_launches() -> int:
