@@ -139,6 +139,26 @@ int eels_solve(eels_ctx* ctx, const eels_opts* opts, int n_energy, const double*
                double* p_eels, double* p_cl, double* p_ext, double* p_abs,
                eels_c128* p_out, eels_point_stats* stats);
 
+/*
+ * Asynchronous form of eels_solve.  The inputs are copied before return; the
+ * solve runs on a host thread of the library, on the context's stream.  The
+ * outputs are written into the caller's buffers (same meaning and layout as
+ * eels_solve) while the job runs: they must stay allocated, and neither they
+ * nor the context may be used, until eels_job_wait returns.  Returns
+ * EELS_E_INVALID_ARG for missing arguments; every other error of the solve is
+ * returned by eels_job_wait.
+ */
+typedef struct eels_job eels_job;
+int eels_solve_async(eels_ctx* ctx, const eels_opts* opts, int n_energy, const double* energy_eV,
+                     int n_mat, const eels_c128* eps_p, const eels_c128* eps_h,
+                     int n_beam, const eels_beam* beams,
+                     double* p_eels, double* p_cl, double* p_ext, double* p_abs,
+                     eels_c128* p_out, eels_point_stats* stats, eels_job** job);
+/* *done = 1 once the job has finished (non-blocking). */
+int eels_job_poll(eels_job* job, int* done);
+/* Block until the job finishes, free it, and return the eels_solve code. */
+int eels_job_wait(eels_job* job);
+
 /* Device-memory footprint (bytes) eels_solve would allocate for a batch of
  * n_systems (energy, beam) systems of this grid under these options. */
 int eels_query_footprint(const eels_grid* grid, const eels_opts* opts, int n_systems, size_t* bytes);

@@ -284,6 +284,205 @@ template void launch_qmr_init<double>(const KrylovArgs<double>&, cudaStream_t);
 template void launch_qmr_post_matvec<float>(const KrylovArgs<float>&, int, bool, cudaStream_t);
 template void launch_qmr_post_matvec<double>(const KrylovArgs<double>&, int, bool, cudaStream_t);
 
+// ------------------------------------------------------------- BiCGStab
+// van der Vorst (SIAM J. Sci. Stat. Comput. 13 (1992) 631) with the shadow
+// residual r^ = r0 and the unconjugated form r^T y for rho and alpha (the
+// complex-symmetric variant); omega minimises ||s - omega t|| with the
+// conjugated inner product.  Per iteration:
+//   v = A p, alpha = rho / r^T v, s = r - alpha v, t = A s,
+//   omega = (t^H s) / (t^H t), x += alpha p + omega s, r = s - omega t,
+//   rho' = r^T r, beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
+
+// part[s][blk] = (Re sum conj(a) b, Im, sum |a|^2, 0)
+template <typename Rl>
+__global__ void k_dotc(int n3, int nblk, const cx<Rl>* __restrict__ a, const cx<Rl>* __restrict__ b, double* part,
+                       const int* active) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    if (active && !active[s]) return;
+    const size_t off = (size_t)s * n3;
+    const int i0 = blk * RED_CHUNK, i1 = min(n3, i0 + RED_CHUNK);
+    Rl v[4] = {0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const cx<Rl> x = a[off + i], y = b[off + i];
+        v[0] += x.x * y.x + x.y * y.y;
+        v[1] += x.x * y.y - x.y * y.x;
+        v[2] += x.x * x.x + x.y * x.y;
+    }
+    block_sum<Rl, 4>(v);
+    if (threadIdx.x == 0) {
+        double* p = part + ((size_t)s * nblk + blk) * 4;
+        p[0] = v[0]; p[1] = v[1]; p[2] = v[2]; p[3] = 0.0;
+    }
+}
+
+// r^ = r, p = r, x = 0
+template <typename Rl>
+__global__ void k_bicg_copy(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y;
+    if (!k.active[s]) return;
+    const size_t off = (size_t)s * k.n3;
+    const cx<Rl> z = mk<cx<Rl>>(0.0, 0.0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x) {
+        const cx<Rl> r = k.R[off + i];
+        k.Rh[off + i] = r;
+        k.Pb[off + i] = r;
+        k.X[off + i] = z;
+    }
+}
+
+template <typename Rl>
+__global__ void k_bicg_start(KrylovArgs<Rl> k) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.S || !k.active[s]) return;
+    double o[4];
+    sum_parts(k.part_a, s, k.nblk, o);     // (r.r, |r|^2)
+    BicgState b;
+    b.rho = make_double2(o[0], o[1]);
+    b.bnorm = sqrt(o[2]);
+    b.alpha = b.omega = b.beta = make_double2(0, 0);
+    b.res = 1.0;
+    b.iters = 0;
+    b.status = 0;
+    if (!(b.bnorm > 0.0)) {       // zero right-hand side: x = 0 is exact
+        b.status = 1;
+        b.res = 0.0;
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+    }
+    k.bicg[s] = b;
+}
+
+// alpha = rho / r^T v ; s = r - alpha v (into R)
+template <typename Rl>
+__global__ void k_bicg_s(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y;
+    if (!k.active[s]) return;
+    __shared__ double2 al;
+    if (threadIdx.x == 0) {
+        double o[4];
+        sum_parts(k.part_a, s, k.nblk, o);
+        const double2 rv = make_double2(o[0], o[1]);
+        al = (abs2_(rv) > 0.0) ? cdiv(k.bicg[s].rho, rv) : make_double2(0, 0);
+        if (blockIdx.x == 0) k.bicg[s].alpha = al;
+    }
+    __syncthreads();
+    const cx<Rl> a = cvt<cx<Rl>>(al);
+    const size_t off = (size_t)s * k.n3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x)
+        k.R[off + i] = k.R[off + i] - a * k.Vb[off + i];
+}
+
+// omega = t^H s / t^H t ; x += alpha p + omega s ; r = s - omega t ; partials of r^.r and |r|^2
+template <typename Rl>
+__global__ void k_bicg_x(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    if (!k.active[s]) return;
+    __shared__ double2 sc[2];
+    if (threadIdx.x == 0) {
+        double o[4];
+        sum_parts(k.part_b, s, k.nblk, o);
+        sc[0] = k.bicg[s].alpha;
+        sc[1] = o[2] > 0.0 ? make_double2(o[0] / o[2], o[1] / o[2]) : make_double2(0, 0);
+        if (blk == 0) k.bicg[s].omega = sc[1];
+    }
+    __syncthreads();
+    const cx<Rl> al = cvt<cx<Rl>>(sc[0]), om = cvt<cx<Rl>>(sc[1]);
+    const size_t off = (size_t)s * k.n3;
+    const int i0 = blk * RED_CHUNK, i1 = min(k.n3, i0 + RED_CHUNK);
+    Rl acc[4] = {0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const cx<Rl> sv = k.R[off + i];
+        k.X[off + i] = k.X[off + i] + al * k.Pb[off + i] + om * sv;
+        const cx<Rl> r = sv - om * k.Tb[off + i];
+        k.R[off + i] = r;
+        const cx<Rl> h = k.Rh[off + i];
+        acc[0] += h.x * r.x - h.y * r.y;
+        acc[1] += h.x * r.y + h.y * r.x;
+        acc[2] += r.x * r.x + r.y * r.y;
+    }
+    block_sum<Rl, 4>(acc);
+    if (threadIdx.x == 0) {
+        double* p = k.part_a + ((size_t)s * k.nblk + blk) * 4;
+        p[0] = acc[0]; p[1] = acc[1]; p[2] = acc[2]; p[3] = 0.0;
+    }
+}
+
+template <typename Rl>
+__global__ void k_bicg_step(KrylovArgs<Rl> k) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.S) return;
+    if (!k.active[s]) { k.upd[s] = 0; return; }
+    BicgState b = k.bicg[s];
+    double o[4];
+    sum_parts(k.part_a, s, k.nblk, o);
+    const double2 rho_n = make_double2(o[0], o[1]);
+    b.res = sqrt(o[2]) / b.bnorm;
+    b.iters += 1;
+    int next = 1;
+    const double eps = k.eps_sys ? k.eps_sys[s] : k.eps;
+    if (b.res <= eps) { b.status = 1; next = 0; }
+    else if (b.iters >= k.max_iter) { b.status = 2; next = 0; }
+    else if (!(abs2_(b.omega) > 0.0) || !(abs2_(b.rho) > 0.0) || !(b.res == b.res)) { b.status = 3; next = 0; }
+    if (next) {
+        b.beta = cdiv(rho_n, b.rho) * cdiv(b.alpha, b.omega);
+        b.rho = rho_n;
+    }
+    k.bicg[s] = b;
+    k.upd[s] = next;
+    if (!next) {
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+    }
+}
+
+// p = r + beta (p - omega v)
+template <typename Rl>
+__global__ void k_bicg_p(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y;
+    if (!k.upd[s]) return;
+    const cx<Rl> be = cvt<cx<Rl>>(k.bicg[s].beta), om = cvt<cx<Rl>>(k.bicg[s].omega);
+    const size_t off = (size_t)s * k.n3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x)
+        k.Pb[off + i] = k.R[off + i] + be * (k.Pb[off + i] - om * k.Vb[off + i]);
+}
+
+template <typename Rl>
+void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
+    count_launch();
+    k_bicg_copy<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
+    count_launch();
+    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.R, k.R, k.part_a, k.active);
+    count_launch();
+    k_bicg_start<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+}
+
+template <typename Rl>
+void launch_bicg_stage1(const KrylovArgs<Rl>& k, cudaStream_t st) {
+    count_launch();
+    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.Rh, k.Vb, k.part_a, k.active);
+    count_launch();
+    k_bicg_s<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
+}
+
+template <typename Rl>
+void launch_bicg_stage2(const KrylovArgs<Rl>& k, cudaStream_t st) {
+    count_launch();
+    k_dotc<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.Tb, k.R, k.part_b, k.active);
+    count_launch();
+    k_bicg_x<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k);
+    count_launch();
+    k_bicg_step<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    count_launch();
+    k_bicg_p<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
+}
+
+template void launch_bicg_init<float>(const KrylovArgs<float>&, cudaStream_t);
+template void launch_bicg_init<double>(const KrylovArgs<double>&, cudaStream_t);
+template void launch_bicg_stage1<float>(const KrylovArgs<float>&, cudaStream_t);
+template void launch_bicg_stage1<double>(const KrylovArgs<double>&, cudaStream_t);
+template void launch_bicg_stage2<float>(const KrylovArgs<float>&, cudaStream_t);
+template void launch_bicg_stage2<double>(const KrylovArgs<double>&, cudaStream_t);
+
 
 // ------------------------------------------------------- FP64 refinement
 __global__ void k_rhs_init(LatticeDev L, int S, const double2* e, const double2* coef, double2* b, double2* x, double2* r) {

@@ -159,6 +159,20 @@ void fill_info(const Job* j, eels_job_info* info) {
 
 }  // namespace
 
+// A single asynchronous eels_solve: copies of the inputs, the thread that
+// runs it, and its return code.
+struct eels_job {
+    eels_opts opts{};
+    std::vector<double> energies;
+    std::vector<eels_c128> eps_p, eps_h;
+    std::vector<eels_beam> beams;
+    int n_mat = 0;
+    std::thread worker;
+    std::mutex mu;
+    bool done = false;
+    int code = EELS_OK;
+};
+
 extern "C" {
 
 int eels_server_create(eels_server** out, const eels_server_opts* o) {
@@ -282,6 +296,51 @@ void eels_server_destroy(eels_server* s) {
     s->cv.notify_all();
     for (auto& t : s->workers) t.join();
     delete s;
+}
+
+// ---- one request on the caller's context, in a host thread ----
+
+int eels_solve_async(eels_ctx* ctx, const eels_opts* opts, int n_energy, const double* energy_eV, int n_mat,
+                     const eels_c128* eps_p, const eels_c128* eps_h, int n_beam, const eels_beam* beams,
+                     double* p_eels, double* p_cl, double* p_ext, double* p_abs, eels_c128* p_out,
+                     eels_point_stats* stats, eels_job** job) {
+    if (!job) return EELS_E_INVALID_ARG;
+    *job = nullptr;
+    if (!ctx || !opts || n_energy <= 0 || n_beam <= 0 || n_mat <= 0 || !energy_eV || !eps_p || !eps_h || !beams ||
+        !p_eels)
+        return EELS_E_INVALID_ARG;
+    auto* j = new eels_job();
+    j->opts = *opts;
+    j->energies.assign(energy_eV, energy_eV + n_energy);
+    j->eps_p.assign(eps_p, eps_p + (size_t)n_energy * n_mat);
+    j->eps_h.assign(eps_h, eps_h + n_energy);
+    j->beams.assign(beams, beams + n_beam);
+    j->n_mat = n_mat;
+    j->worker = std::thread([j, ctx, p_eels, p_cl, p_ext, p_abs, p_out, stats] {
+        const int code = eels_solve(ctx, &j->opts, (int)j->energies.size(), j->energies.data(), j->n_mat,
+                                    j->eps_p.data(), j->eps_h.data(), (int)j->beams.size(), j->beams.data(), p_eels,
+                                    p_cl, p_ext, p_abs, p_out, stats);
+        std::lock_guard<std::mutex> lk(j->mu);
+        j->code = code;
+        j->done = true;
+    });
+    *job = j;
+    return EELS_OK;
+}
+
+int eels_job_poll(eels_job* job, int* done) {
+    if (!job || !done) return EELS_E_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(job->mu);
+    *done = job->done ? 1 : 0;
+    return EELS_OK;
+}
+
+int eels_job_wait(eels_job* job) {
+    if (!job) return EELS_E_INVALID_ARG;
+    job->worker.join();
+    const int code = job->code;
+    delete job;
+    return code;
 }
 
 }  // extern "C"

@@ -23,7 +23,7 @@ struct QmrState {
 
 // BiCGStab per-system scalars (FP64).
 struct BicgState {
-    double2 rho, alpha, omega;
+    double2 rho, alpha, omega, beta;
     double bnorm, res;
     int iters, status;
 };
@@ -59,9 +59,11 @@ template <typename Rl> void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_
 template <typename Rl> void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, bool dot_done, cudaStream_t st);
 // BiCGStab (van der Vorst 1992) with the unconjugated shadow residual
 // r^ = r0 (complex-symmetric form); rhs in R, X = 0.
+// Vector roles: R (residual; the rhs on entry, S = R - alpha V overwrites
+// it), Rh (shadow), Pb (direction), Vb = A Pb, Tb = A S, X (iterate).
 template <typename Rl> void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st);
 template <typename Rl> void launch_bicg_stage1(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Vb = A Pb
-template <typename Rl> void launch_bicg_stage2(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Tb = A Sb
+template <typename Rl> void launch_bicg_stage2(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Tb = A S
 
 // ---- FP64 refinement helpers (vectors [S][n3]) ----
 // b = coef[mat] * e; x = 0; r = b

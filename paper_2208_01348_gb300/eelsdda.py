@@ -84,6 +84,11 @@ _sig = {
     "eels_padded_dims": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "eels_solve": (C.c_int, [_P, C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp, C.c_int,
                              C.POINTER(eels_beam), _dp, _dp, _dp, _dp, _cp, C.POINTER(eels_point_stats)]),
+    "eels_solve_async": (C.c_int, [_P, C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp, C.c_int,
+                                   C.POINTER(eels_beam), _dp, _dp, _dp, _dp, _cp, C.POINTER(eels_point_stats),
+                                   C.POINTER(_P)]),
+    "eels_job_poll": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "eels_job_wait": (C.c_int, [_P]),
     "eels_query_footprint": (C.c_int, [C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, C.POINTER(C.c_size_t)]),
     "eels_bessel_k01_dev": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "eels_incident_field": (C.c_int, [_P, C.c_double, C.c_double, eels_c128, eels_beam, _cp, _cp]),
@@ -194,30 +199,77 @@ class SolveResult:
     code: int
 
 
+class _SolveCall:
+    """Marshalled arguments and output buffers of one eels_solve call."""
+
+    def __init__(self, ctx, opts, energies_eV, eps_p, eps_h, beams_nm, want_cl, want_ext, want_abs, want_p):
+        self.e = np.ascontiguousarray(energies_eV, dtype=np.float64).ravel()
+        ne = len(self.e)
+        self.ep = _c128(eps_p).reshape(ne, -1)
+        self.eh = _c128(eps_h).ravel()
+        bm = np.ascontiguousarray(beams_nm, dtype=np.float64).reshape(-1, 2)
+        nb = len(bm)
+        self.beams = (eels_beam * nb)(*[eels_beam(float(x), float(y)) for x, y in bm])
+        self.out = {k: np.zeros((ne, nb)) for k in ("eels", "cl", "ext", "abs")}
+        self.want = (want_cl, want_ext, want_abs, want_p)
+        n = eels_num_dipoles(ctx)
+        self.p = np.zeros((ne, nb, n, 3), dtype=np.complex128) if want_p else None
+        self.st = (eels_point_stats * (ne * nb))()
+        self.shape = (ne, nb)
+        self.opts = opts
+
+    def args(self, ctx):
+        o, (wc, we, wa, wp) = self.out, self.want
+        return (ctx, C.byref(self.opts), self.shape[0], self.e.ctypes.data_as(_dp), self.ep.shape[1], _cptr(self.ep),
+                _cptr(self.eh), self.shape[1], self.beams, _dptr(o["eels"]), _dptr(o["cl"]) if wc else None,
+                _dptr(o["ext"]) if we else None, _dptr(o["abs"]) if wa else None, _cptr(self.p) if wp else None,
+                self.st)
+
+    def result(self, code, ctx, raise_not_converged):
+        if code != EELS_OK and not (code == EELS_E_NOT_CONVERGED and not raise_not_converged):
+            _check(code, ctx)
+        ne, nb = self.shape
+        wc, we, wa, _ = self.want
+        sa = np.array([(s.iters, s.refinements, s.residual, s.converged) for s in self.st]).reshape(ne, nb, 4)
+        o = self.out
+        return SolveResult(o["eels"], o["cl"] if wc else None, o["ext"] if we else None, o["abs"] if wa else None,
+                           self.p, sa[..., 0].astype(int), sa[..., 1].astype(int), sa[..., 2],
+                           sa[..., 3].astype(bool), code)
+
+
 def eels_solve(ctx, opts: eels_opts, energies_eV, eps_p, eps_h, beams_nm, want_cl=True, want_ext=True,
                want_abs=True, want_p=False, raise_not_converged=True) -> SolveResult:
     """energies [E]; eps_p [E][n_mat]; eps_h [E]; beams [B][2] -> arrays [E][B]."""
-    e = np.ascontiguousarray(energies_eV, dtype=np.float64).ravel()
-    ne = len(e)
-    ep = _c128(eps_p).reshape(ne, -1)
-    eh = _c128(eps_h).ravel()
-    bm = np.ascontiguousarray(beams_nm, dtype=np.float64).reshape(-1, 2)
-    nb = len(bm)
-    beams = (eels_beam * nb)(*[eels_beam(float(x), float(y)) for x, y in bm])
-    out = {k: np.zeros((ne, nb)) for k in ("eels", "cl", "ext", "abs")}
-    n = eels_num_dipoles(ctx)
-    p = np.zeros((ne, nb, n, 3), dtype=np.complex128) if want_p else None
-    st = (eels_point_stats * (ne * nb))()
-    code = _lib.eels_solve(ctx, C.byref(opts), ne, e.ctypes.data_as(_dp), ep.shape[1], _cptr(ep), _cptr(eh), nb, beams,
-                           _dptr(out["eels"]), _dptr(out["cl"]) if want_cl else None,
-                           _dptr(out["ext"]) if want_ext else None, _dptr(out["abs"]) if want_abs else None,
-                           _cptr(p) if want_p else None, st)
-    if code != EELS_OK and not (code == EELS_E_NOT_CONVERGED and not raise_not_converged):
-        _check(code, ctx)
-    sa = np.array([(s.iters, s.refinements, s.residual, s.converged) for s in st]).reshape(ne, nb, 4)
-    return SolveResult(out["eels"], out["cl"] if want_cl else None, out["ext"] if want_ext else None,
-                       out["abs"] if want_abs else None, p, sa[..., 0].astype(int), sa[..., 1].astype(int),
-                       sa[..., 2], sa[..., 3].astype(bool), code)
+    call = _SolveCall(ctx, opts, energies_eV, eps_p, eps_h, beams_nm, want_cl, want_ext, want_abs, want_p)
+    return call.result(_lib.eels_solve(*call.args(ctx)), ctx, raise_not_converged)
+
+
+class SolveJob:
+    """A running eels_solve_async; its buffers live until wait() returns."""
+
+    def __init__(self, ctx, call: _SolveCall, handle):
+        self._ctx, self._call, self._h = ctx, call, handle
+
+    def poll(self) -> bool:
+        d = C.c_int()
+        _check(_lib.eels_job_poll(self._h, C.byref(d)))
+        return bool(d.value)
+
+    def wait(self, raise_not_converged=True) -> SolveResult:
+        if self._h is None:
+            raise RuntimeError("job already waited")
+        code = _lib.eels_job_wait(self._h)
+        self._h = None
+        return self._call.result(code, self._ctx, raise_not_converged)
+
+
+def eels_solve_async(ctx, opts: eels_opts, energies_eV, eps_p, eps_h, beams_nm, want_cl=True, want_ext=True,
+                     want_abs=True, want_p=False) -> SolveJob:
+    """Start eels_solve on a library thread; SolveJob.wait() returns its SolveResult."""
+    call = _SolveCall(ctx, opts, energies_eV, eps_p, eps_h, beams_nm, want_cl, want_ext, want_abs, want_p)
+    h = _P()
+    _check(_lib.eels_solve_async(*call.args(ctx), C.byref(h)), ctx)
+    return SolveJob(ctx, call, h)
 
 
 def eels_query_footprint(occ: np.ndarray, d_nm: float, opts: eels_opts, n_systems: int) -> int:

@@ -222,3 +222,34 @@ def test_invalid_inputs_raise(dd, ctx):
     with pytest.raises(dd.EelsError) as e:
         dd.eels_set_grid(ctx, np.zeros((3, 3, 3), np.uint8), 1.0)
     assert e.value.code == dd.EELS_E_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_bicgstab_matches_lu(dd, ctx, prec):
+    """The BiCGStab inner solver reaches the same solution as LU (Cherenkov
+    absorbing host replica, 3 energies, and the small gold sphere)."""
+    for w in (I.reduced(I.config_cherenkov(), 12 / 64, n_energy=3), I.config_small_sphere()):
+        g = w.grid
+        dd.eels_set_grid(ctx, g.occ, g.d_nm)
+        o = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=getattr(dd, "EELS_" + prec), solver=dd.EELS_BICGSTAB,
+                                 eps_it=1e-12 if prec == "FP64" else 1e-8)
+        res = dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, w.beams_nm, want_p=True)
+        assert res.converged.all()
+        tol = 1e-10 if prec == "FP64" else 1e-4
+        for ie in range(len(w.energies_eV)):
+            _check_point(res, ie, 0, _oracle(w, ie, 0), tol, tol)
+
+
+def test_async_solve_matches_blocking_solve(dd, ctx):
+    """eels_solve_async gives the same bits as eels_solve on the same context."""
+    w = I.reduced(I.config_spectrum(), 10 / 32, n_energy=3)
+    ref = _solve(dd, ctx, w, dd.EELS_MIXED, want_p=True, eps=1e-8)
+    o = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=dd.EELS_MIXED, eps_it=1e-8)
+    job = dd.eels_solve_async(ctx, o, w.energies_eV, w.eps_p, w.eps_h, w.beams_nm, want_p=True)
+    import time
+    t_end = time.time() + 120.0
+    while not job.poll() and time.time() < t_end:
+        time.sleep(0.01)
+    res = job.wait()
+    for a, b in ((res.p_eels, ref.p_eels), (res.p_cl, ref.p_cl), (res.p_ext, ref.p_ext), (res.p, ref.p)):
+        assert np.array_equal(a, b)

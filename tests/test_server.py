@@ -29,7 +29,9 @@ def _request(n, n_energy, n_beam):
 
 def test_dryrun_admission_respects_budget_and_backfills(dd):
     o = dd.eels_default_opts()
-    occ_big, d, e, ep, eh, b = _request(24, 8, 4)
+    # 64 x 8 points: the dry run holds each big request's slot for ~10 ms, far
+    # longer than submitting the next requests takes
+    occ_big, d, e, ep, eh, b = _request(24, 64, 8)
     fp_big = dd.eels_query_footprint(occ_big, d, o, 1)     # smallest batch of the big request
     budget = int(fp_big * 1.5)       # room for one big request at a time, plus small ones
     srv = dd.eels_server_create(hbm_budget=budget, max_concurrent=2, flags=dd.EELS_SERVER_DRYRUN)
