@@ -298,7 +298,7 @@ def main():
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="time only the FFT matvec on this many systems of the workload (profiling)")
     ap.add_argument("--serve-requests", type=int, default=16)
-    ap.add_argument("--serve-concurrency", type=int, default=4)
+    ap.add_argument("--serve-concurrency", type=int, default=8)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -334,6 +334,11 @@ def main():
         if dist:
             dist.barrier()
 
+    if world > 1:
+        # weak scaling: every rank solves a full workload of its own (distinct
+        # beam positions, same amount of work); no data moves between ranks
+        from paper_2208_01348_gb300 import sharding
+        w.beams_nm = np.array(sharding.weak_scaling_beams(w.beams_nm, rank))
     stream = torch.cuda.current_stream()
     ctx = dd.eels_create(local, stream.cuda_stream)
     g = w.grid

@@ -230,7 +230,7 @@ struct eels_ctx {
     // workspace
     DevBuf e64, b64, x64, r64, y64, U, u64, u32;
     DevBuf kv[7];                                          // Krylov vectors V0 V1 P0 P1 P2 W X
-    DevBuf part_a, part_b, qmr, active, upd, counters, outer, res, rnorm, eps_sys;
+    DevBuf part_a, part_b, qmr, bicg, active, upd, counters, outer, res, rnorm, eps_sys;
     DevBuf sysf, coef, diag, wabs, wdv, slot, kappa_sys;
     DevBuf G, Dr64, Dr32, kappa_slot;
     DevBuf lpart, lsums, fpart, fsums, dirs, wts;
@@ -245,7 +245,7 @@ struct eels_ctx {
 
     std::vector<DevBuf*> buffers() {
         std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
-                                  &part_a, &part_b, &qmr, &active, &upd, &counters, &outer, &res, &rnorm, &eps_sys,
+                                  &part_a, &part_b, &qmr, &bicg, &active, &upd, &counters, &outer, &res, &rnorm, &eps_sys,
                                   &sysf, &coef, &diag, &wabs, &wdv, &slot, &kappa_sys, &G, &Dr64, &Dr32, &kappa_slot,
                                   &lpart, &lsums, &fpart, &fsums, &dirs, &wts};
         for (auto& b : kv) v.push_back(&b);
@@ -447,6 +447,10 @@ KrylovArgs<Rl> krylov_args(eels_ctx* c, int S, const eels_opts* o, double eps) {
     k.W = c->kv[5].as<cx<Rl>>(); k.X = c->kv[6].as<cx<Rl>>();
     k.part_a = c->part_a.as<double>(); k.part_b = c->part_b.as<double>();
     k.qmr = c->qmr.as<QmrState>();
+    // BiCGStab roles in the same seven buffers (the rhs arrives in kv[1], the iterate is kv[6])
+    k.R = c->kv[1].as<cx<Rl>>(); k.Rh = c->kv[0].as<cx<Rl>>(); k.Pb = c->kv[2].as<cx<Rl>>();
+    k.Vb = c->kv[3].as<cx<Rl>>(); k.Tb = c->kv[4].as<cx<Rl>>(); k.Sb = k.R;
+    k.bicg = c->bicg.as<BicgState>();
     k.active = c->active.as<int>(); k.upd = c->upd.as<int>();
     k.n_active = c->counters.as<int>();
     k.eps = eps;
@@ -472,24 +476,27 @@ template <typename Rl> const cx<Rl>* dr_of(eels_ctx* c);
 template <> const float2* dr_of<float>(eels_ctx* c) { return c->Dr32.as<float2>(); }
 template <> const double2* dr_of<double>(eels_ctx* c) { return c->Dr64.as<double2>(); }
 
-// Inner Krylov solve on the active systems; returns the number of iterations run.
+// Inner Krylov solve (QMR or BiCGStab) on the active systems; returns the
+// number of iterations run.
 template <typename Rl>
-int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
+int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
     cudaStream_t st = c->stream;
     KrylovArgs<Rl> k = krylov_args<Rl>(c, S, o, eps);
+    const bool bicg = o->solver == EELS_BICGSTAB;
     // the three-pass matvec also returns the per-slab partial sums of v^T (A v)
-    const bool fused = matvec_passes(c->L, sizeof(Rl) == 8) == 3;
+    const bool fused = !bicg && matvec_passes(c->L, sizeof(Rl) == 8) == 3;
     k.nblk_a = fused ? 3 * c->L.Nx : k.nblk;
-    launch_qmr_init<Rl>(k, st);
+    if (bicg) launch_bicg_init<Rl>(k, st);
+    else launch_qmr_init<Rl>(k, st);
     CK(cudaGetLastError());
-    constexpr int CHUNK = 6;   // period of the vector-slot rotation (2 and 3)
+    constexpr int CHUNK = 6;   // period of the QMR vector-slot rotation (2 and 3)
     // every pointer and scalar baked into the captured kernels
     std::vector<const void*> key = {k.V[0], k.V[1], k.P[0], k.P[1], k.P[2], k.W, k.X, c->U.p, dr_of<Rl>(c),
                                     (const void*)(size_t)S, (const void*)(size_t)sizeof(Rl),
                                     (const void*)(size_t)inner_cap(o, sizeof(Rl) == 4), c->coef.p, c->diag.p, c->slot.p, c->qmr.p,
                                     c->part_a.p, c->part_b.p, c->active.p, c->upd.p, c->counters.p, c->eps_sys.p,
-                                    c->cellmap.p};
-    // eps is read inside k_qmr_step from the kernel argument: make it part of the key
+                                    c->cellmap.p, c->bicg.p, (const void*)(size_t)bicg};
+    // eps is read inside the step kernel from the kernel argument: make it part of the key
     double epsv = eps;
     const void* ek;
     std::memcpy(&ek, &epsv, sizeof(ek));
@@ -500,6 +507,13 @@ int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         g_capturing = true;
         for (int n = 1; n <= CHUNK; ++n) {
+            if (bicg) {
+                launch_matvec<Rl>(c->L, mv_args<Rl>(c, S, k.Pb, k.Vb, dr_of<Rl>(c), k.active, true), st);
+                launch_bicg_stage1<Rl>(k, st);
+                launch_matvec<Rl>(c->L, mv_args<Rl>(c, S, k.R, k.Tb, dr_of<Rl>(c), k.active, true), st);
+                launch_bicg_stage2<Rl>(k, st);
+                continue;
+            }
             MatvecArgs<Rl> a = mv_args<Rl>(c, S, k.V[n & 1], k.W, dr_of<Rl>(c), k.active, true);
             a.dot_part = fused ? k.part_a : nullptr;
             launch_matvec<Rl>(c->L, a, st);
@@ -522,21 +536,31 @@ int inner_qmr(eels_ctx* c, int S, const eels_opts* o, double eps) {
         c->graph_key = key;
     }
     int it = 0;
+    // The host reads the number of active systems between bursts of graph
+    // replays; a burst grows from 1 to 8 replays as the solve goes on (a
+    // replay after every system has converged only launches empty blocks).
     const int max_chunks = inner_cap(o, sizeof(Rl) == 4) / CHUNK + 2;
-    for (int ch = 0; ch < max_chunks; ++ch) {
+    int burst = 1;
+    for (int ch = 0; ch < max_chunks;) {
         CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (*c->pinned <= 0) break;
-        CK(cudaGraphLaunch(c->graph, st));
-        g_kernel_launches += c->graph_kernels;
-        it += CHUNK;
+        for (int b = 0; b < burst && ch < max_chunks; ++b, ++ch) {
+            CK(cudaGraphLaunch(c->graph, st));
+            g_kernel_launches += c->graph_kernels;
+            it += CHUNK;
+        }
+        burst = std::min(8, burst * 2);
     }
     return it;
 }
 
+// Up to max_rounds refinement rounds with inner solves in precision Rl, on
+// the systems whose FP64 residual is still above eps_it.  Returns how many
+// systems are still above it after the last residual check.
 template <typename Rl>
-void refine_batch(eels_ctx* c, int S, const eels_opts* o, std::vector<int>& iters, std::vector<int>& refin,
-                  std::vector<double>& resid) {
+int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::vector<int>& iters,
+                  std::vector<int>& refin) {
     cudaStream_t st = c->stream;
     const int n3 = 3 * c->N;
     const int nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
@@ -546,31 +570,87 @@ void refine_batch(eels_ctx* c, int S, const eels_opts* o, std::vector<int>& iter
     // solve is asked for 0.5 eps_it / res, the reduction that reaches eps_it
     const double eps_floor = (sizeof(Rl) == 4) ? std::max(o->eps_inner, 1e-7) : 1e-15;
     const double safety = (sizeof(Rl) == 4) ? 0.3 : 0.5;
-    const double eps_inner = eps_floor;
-    const int max_outer = (sizeof(Rl) == 4) ? 200 : 8;
     std::vector<QmrState> qh(S);
-    for (int outer_it = 0; outer_it <= max_outer; ++outer_it) {
+    std::vector<BicgState> bh(S);
+    std::vector<int> outer_h(S), slow_rounds(S, 0), stalled(S, 0);
+    std::vector<double> res_h(S, 1.0), res_prev(S, 1.0);
+    int left = 0;
+    for (int round = 0; round <= max_rounds; ++round) {
         launch_norms2(S, n3, nblk, c->r64.as<double2>(), c->b64.as<double2>(), c->part_a.as<double>(), st);
         launch_residual_check(S, nblk, c->part_a.as<double>(), o->eps_it, eps_floor, safety, c->res.as<double>(),
                               c->rnorm.as<double>(), c->outer.as<int>(), n_outer, c->eps_sys.as<double>(), st);
         CK(cudaMemcpyAsync(c->pinned, n_outer, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (*c->pinned == 0 || outer_it == max_outer) break;
+        left = *c->pinned;
+        if (left == 0 || round == max_rounds) break;
+        if (sizeof(Rl) == 4) {
+            // FP32 rounding can stall an inner solve: a system whose FP64
+            // residual fell by less than 2x in each of the last two rounds
+            // leaves the FP32 rounds (the FP64 rounds that follow take it);
+            // the other systems go on in FP32
+            CK(cudaMemcpyAsync(res_h.data(), c->res.p, S * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(outer_h.data(), c->outer.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            int running = 0;
+            bool masked = false;
+            for (int s = 0; s < S; ++s) {
+                const bool slow = outer_h[s] && round > 0 && res_h[s] > 0.5 * res_prev[s];
+                slow_rounds[s] = slow ? slow_rounds[s] + 1 : 0;
+                if (slow_rounds[s] >= 2) stalled[s] = 1;
+                if (stalled[s] && outer_h[s]) {
+                    outer_h[s] = 0;
+                    masked = true;
+                }
+                running += outer_h[s];
+                res_prev[s] = res_h[s];
+            }
+            if (running == 0) break;
+            if (masked) CK(cudaMemcpyAsync(c->outer.p, outer_h.data(), S * sizeof(int), cudaMemcpyHostToDevice, st));
+        }
         launch_make_inner_rhs<Rl>(S, n3, c->r64.as<double2>(), c->rnorm.as<double>(), c->outer.as<int>(),
                                   c->kv[1].as<cx<Rl>>(), c->active.as<int>(), c->counters.as<int>(), st);
-        inner_qmr<Rl>(c, S, o, eps_inner);
-        CK(cudaMemcpyAsync(qh.data(), c->qmr.p, S * sizeof(QmrState), cudaMemcpyDeviceToHost, st));
-        std::vector<int> outer_h(S);
+        inner_solve<Rl>(c, S, o, eps_floor);
+        if (o->solver == EELS_BICGSTAB) {
+            CK(cudaMemcpyAsync(bh.data(), c->bicg.p, S * sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+        } else {
+            CK(cudaMemcpyAsync(qh.data(), c->qmr.p, S * sizeof(QmrState), cudaMemcpyDeviceToHost, st));
+        }
         CK(cudaMemcpyAsync(outer_h.data(), c->outer.p, S * sizeof(int), cudaMemcpyDeviceToHost, st));
         launch_accumulate<Rl>(S, n3, c->kv[6].as<cx<Rl>>(), c->rnorm.as<double>(), c->outer.as<int>(),
                               c->x64.as<double2>(), st);
+        // new residuals of the systems that took this round; the others keep
+        // x, and y = A x from the round that last changed them
         MatvecArgs<double> a = mv_args<double>(c, S, c->x64.as<double2>(), c->y64.as<double2>(), c->Dr64.as<double2>(),
-                                               nullptr, true);
+                                               c->outer.as<int>(), true);
         launch_matvec<double>(c->L, a, st);
         launch_sub(S, n3, c->b64.as<double2>(), c->y64.as<double2>(), c->r64.as<double2>(), st);
         CK(cudaStreamSynchronize(st));
         for (int s = 0; s < S; ++s)
-            if (outer_h[s]) { iters[s] += qh[s].iters; refin[s] += 1; }
+            if (outer_h[s]) {
+                iters[s] += o->solver == EELS_BICGSTAB ? bh[s].iters : qh[s].iters;
+                refin[s] += 1;
+            }
+    }
+    return left;
+}
+
+// FP64 refinement of a batch.  EELS_MIXED: FP32 inner solves (restarted
+// every inner_max_iter iterations) until every system reaches eps_it or
+// stalls (see refine_rounds) or 30 rounds pass; systems still above eps_it
+// then continue with FP64 inner solves.  Lattices whose padded FFT
+// grid is below 16^3 points go straight to FP64 inner solves: their matvec is
+// bound by launch latency, so FP32 would save nothing and cost iterations.
+// EELS_FP64: FP64 inner solves.
+void refine_batch(eels_ctx* c, int S, const eels_opts* o, bool fp64, std::vector<int>& iters, std::vector<int>& refin,
+                  std::vector<double>& resid) {
+    cudaStream_t st = c->stream;
+    int left = 1;
+    const size_t m_pad = (size_t)c->L.Mx * c->L.My * c->L.Mz;
+    if (!fp64 && m_pad >= (size_t)16 * 16 * 16) left = refine_rounds<float>(c, S, o, 30, iters, refin);
+    if (left > 0) {
+        const size_t kvec64 = (size_t)S * 3 * c->N * sizeof(double2);
+        for (auto& b : c->kv) b.ensure(kvec64);
+        refine_rounds<double>(c, S, o, 8, iters, refin);
     }
     CK(cudaMemcpyAsync(resid.data(), c->res.p, S * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -584,7 +664,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         throw Fail{EELS_E_INVALID_ARG, "solve: NULL input or non-positive counts"};
     if (n_mat < c->max_mat || n_mat > EELS_MAX_MAT) throw Fail{EELS_E_INVALID_ARG, "n_mat does not cover the grid materials"};
     if (o->precision != EELS_FP64 && o->precision != EELS_MIXED) throw Fail{EELS_E_INVALID_ARG, "unknown precision"};
-    if (o->solver != EELS_QMR) throw Fail{EELS_E_UNSUPPORTED, "solver: only EELS_QMR is implemented"};
+    if (o->solver != EELS_QMR && o->solver != EELS_BICGSTAB) throw Fail{EELS_E_INVALID_ARG, "unknown solver"};
     if (!(o->eps_it > 0) || o->max_iter <= 0) throw Fail{EELS_E_INVALID_ARG, "eps_it and max_iter must be positive"};
     if (p_cl && o->n_dir <= 0) throw Fail{EELS_E_INVALID_ARG, "p_cl requested with n_dir = 0"};
     check_beams(c, n_beam, beams);
@@ -641,6 +721,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         c->part_a.ensure((size_t)S * std::max(nblk, 3 * L.Nx) * 4 * sizeof(double));
         c->part_b.ensure((size_t)S * nblk * 4 * sizeof(double));
         c->qmr.ensure((size_t)S * sizeof(QmrState));
+        c->bicg.ensure((size_t)S * sizeof(BicgState));
         c->active.ensure(S * sizeof(int)); c->upd.ensure(S * sizeof(int)); c->outer.ensure(S * sizeof(int));
         c->counters.ensure(64);
         c->res.ensure(S * sizeof(double)); c->rnorm.ensure(S * sizeof(double)); c->eps_sys.ensure(S * sizeof(double));
@@ -687,11 +768,12 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         launch_incident_field(L, S, c->sysf.as<SysField>(), c->e64.as<double2>(), st);
         launch_rhs_init(L, S, c->e64.as<double2>(), c->coef.as<double2>(), c->b64.as<double2>(), c->x64.as<double2>(),
                         c->r64.as<double2>(), st);
+        // y = A x for x = 0: refinement rounds recompute y only for the systems they update
+        CK(cudaMemsetAsync(c->y64.p, 0, (size_t)S * 3 * c->N * sizeof(double2), st));
         CK(cudaGetLastError());
         std::vector<int> it_b(S, 0), rf_b(S, 0);
         std::vector<double> rs_b(S, 0.0);
-        if (fp64) refine_batch<double>(c, S, o, it_b, rf_b, rs_b);
-        else refine_batch<float>(c, S, o, it_b, rf_b, rs_b);
+        refine_batch(c, S, o, fp64, it_b, rf_b, rs_b);
         // losses
         const int lblk = std::max(1, std::min(64, (c->N + 2047) / 2048));
         c->lpart.ensure((size_t)S * lblk * 8 * sizeof(double));

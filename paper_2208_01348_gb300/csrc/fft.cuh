@@ -264,15 +264,18 @@ __device__ __forceinline__ void fft_stage_any(const FftStage sd, const C* tw, In
 // Full transform of NL lines whose inputs are read through ld(line, i) by
 // the first stage and whose outputs are handed to st(line, i, value) by the
 // last stage; the stages in between ping-pong between the shared buffers A
-// and B (element i of line l at l * lstride + i * estride).  The block is
-// synchronised between stages and after the last one.
-template <bool INV, bool LINE_FAST, int NL, typename C, class Ld, class St>
+// and B (element i of line l at l * lstride + i * estride; with PAD8 one
+// padding slot follows every 8 elements, i -> i + i/8, which together with a
+// line stride of 8 mod 16 makes the radix-8 stride-8 scatter of the first
+// stage free of bank conflicts).  The block is synchronised between stages
+// and after the last one.
+template <bool INV, bool LINE_FAST, int NL, bool PAD8 = false, typename C, class Ld, class St>
 __device__ void fft_lines_io(C* A, C* B, int lstride, int estride, const FftPlan& p, const C* tw, Ld ld, St st) {
     auto sm_in = [&](const C* buf) {
-        return [=](int l, int i) { return buf[l * lstride + i * estride]; };
+        return [=](int l, int i) { return buf[l * lstride + (PAD8 ? i + (i >> 3) : i) * estride]; };
     };
     auto sm_out = [&](C* buf) {
-        return [=](int l, int i, C v) { buf[l * lstride + i * estride] = v; };
+        return [=](int l, int i, C v) { buf[l * lstride + (PAD8 ? i + (i >> 3) : i) * estride] = v; };
     };
     if (p.nst == 1) {
         fft_stage_any<INV, LINE_FAST, NL>(p.st[0], tw, ld, st);

@@ -304,7 +304,17 @@ __global__ void k_extract(LatticeDev L, int n_slot, const double2* G, double2* D
 // ---------------------------------------------------------------------------
 // Row stride of the z-transform tile: runs of 8 elements of consecutive rows
 // fall in disjoint bank groups when the stride is 8 mod 16.
-__host__ __device__ __forceinline__ int slab_row_stride(int Mz) { return Mz + ((Mz % 16 == 0) ? 8 : 1); }
+__host__ __device__ __forceinline__ int slab_row_stride(int Mz) {
+    int p = (Mz - 1) + ((Mz - 1) >> 3) + 1;   // padded row length (one slot per 8 elements)
+    while (p % 16 != 8) ++p;
+    return p;
+}
+// Slab buffer S[My][Nz]: rows padded to a multiple of 16 elements, and bit 3
+// of the column index flipped on odd rows, so that the 8-element runs that
+// consecutive rows read or write fall in disjoint banks without widening the
+// rows.
+__host__ __device__ __forceinline__ int slab_s_stride(int Nz) { return (Nz + 15) / 16 * 16; }
+__device__ __forceinline__ int sidx(int y, int z, int sls) { return y * sls + (z ^ ((y & 1) << 3)); }
 
 template <typename Rl, int CW>
 __device__ __forceinline__ void slab_smem(unsigned char* raw, const LatticeDev& L, cx<Rl>*& twy, cx<Rl>*& twz,
@@ -314,7 +324,7 @@ __device__ __forceinline__ void slab_smem(unsigned char* raw, const LatticeDev& 
     twy = reinterpret_cast<C*>(raw);
     twz = twy + L.My;
     S = twz + L.Mz;
-    A = S + L.My * (L.Nz + 1);
+    A = S + L.My * slab_s_stride(L.Nz);
     B = A + scr;
     const C* gy = tw_of<Rl>(L, 1);
     const C* gz = tw_of<Rl>(L, 2);
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_fwd(LatticeDev L, MatvecAr
     const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
     const int My = L.My, Ny = L.Ny, Nz = L.Nz;
-    const int sls = Nz + 1, es = CW + 1, rls = slab_row_stride(L.Mz);
+    const int sls = slab_s_stride(Nz), es = CW + 1, rls = slab_row_stride(L.Mz);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *twy, *twz, *S, *A, *B;
     slab_smem<Rl, CW>(smem_raw, L, twy, twz, S, A, B);
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_fwd(LatticeDev L, MatvecAr
         };
         auto st = [&](int l, int y, C v) {
             const int iz = iz0 + l;
-            if (iz < Nz) S[y * sls + iz] = v;
+            if (iz < Nz) S[sidx(y, iz, sls)] = v;
         };
         fft_lines_io<false, true, CW>(A, B, 1, es, L.py, twy, ld, st);
     }
@@ -357,13 +367,13 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_fwd(LatticeDev L, MatvecAr
     for (int ky0 = 0; ky0 < My; ky0 += CW) {
         auto ld = [&](int l, int z) -> C {
             const int ky = ky0 + l;
-            return (z < Nz && ky < My) ? S[ky * sls + z] : zero;
+            return (z < Nz && ky < My) ? S[sidx(ky, z, sls)] : zero;
         };
         auto st = [&](int l, int z, C v) {
             const int ky = ky0 + l;
             if (ky < My) U[(size_t)ky * row + z] = v;
         };
-        fft_lines_io<false, false, CW>(A, B, rls, 1, L.pz, twz, ld, st);
+        fft_lines_io<false, false, CW, true>(A, B, rls, 1, L.pz, twz, ld, st);
     }
 }
 
@@ -373,7 +383,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
     const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
     const int My = L.My, Ny = L.Ny, Nz = L.Nz;
-    const int sls = Nz + 1, es = CW + 1, rls = slab_row_stride(L.Mz);
+    const int sls = slab_s_stride(Nz), es = CW + 1, rls = slab_row_stride(L.Mz);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *twy, *twz, *S, *A, *B;
     slab_smem<Rl, CW>(smem_raw, L, twy, twz, S, A, B);
@@ -389,9 +399,9 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
         };
         auto st = [&](int l, int z, C v) {
             const int ky = ky0 + l;
-            if (ky < My && z < Nz) S[ky * sls + z] = v;
+            if (ky < My && z < Nz) S[sidx(ky, z, sls)] = v;
         };
-        fft_lines_io<true, false, CW>(A, B, rls, 1, L.pz, twz, ld, st);
+        fft_lines_io<true, false, CW, true>(A, B, rls, 1, L.pz, twz, ld, st);
     }
     // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
     for (int iz0 = 0; iz0 < Nz; iz0 += CW) {
         auto ld = [&](int l, int y) -> C {
             const int iz = iz0 + l;
-            return iz < Nz ? S[y * sls + iz] : zero;
+            return iz < Nz ? S[sidx(y, iz, sls)] : zero;
         };
         auto st = [&](int l, int y, C v) {
             const int iz = iz0 + l;
@@ -451,6 +461,8 @@ template <typename Rl> static size_t smem_axis(int Lf, int W, int axis) {
 
 template <typename K> static void allow_smem(K kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    // these kernels keep their working tiles in shared memory: give it the whole carveout
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // Pick the widest tile whose shared memory fits a budget that leaves room
@@ -506,7 +518,7 @@ static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStrea
 
 template <typename Rl, int CW> static size_t smem_slab(const LatticeDev& L) {
     const size_t scr = (size_t)std::max(L.My * (CW + 1), CW * slab_row_stride(L.Mz));
-    return ((size_t)L.My + L.Mz + (size_t)L.My * (L.Nz + 1) + 2 * scr) * sizeof(cx<Rl>);
+    return ((size_t)L.My + L.Mz + (size_t)L.My * slab_s_stride(L.Nz) + 2 * scr) * sizeof(cx<Rl>);
 }
 
 // Widest column tile whose fused-slab shared memory fits one block (0: none).
@@ -534,10 +546,10 @@ template <typename Rl> static void slab_launch_any(const LatticeDev& L, const Ma
     else slab_launch<Rl, 8>(L, a, inv, st);
 }
 
-// The x pass is latency-bound on its global loads: prefer the tile that
-// keeps four blocks resident per SM.
+// Widest x-pass tile (W lines per component) whose two buffers fit a
+// quarter of an SM's shared memory, so that four blocks are resident.
 template <typename Rl> static int pick_xpass_w(const LatticeDev& L) {
-    for (int W : {32, 16})
+    for (int W : {32, 16, 8})
         if (smem_xpass<Rl>(L, W) <= 56 * 1024) return W;
     return pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
 }
@@ -600,12 +612,12 @@ int matvec_passes(const LatticeDev& L, bool fp64) {
 
 size_t matvec_smem_bytes(const LatticeDev& L, bool fp64) {
     if (fp64) {
-        const int wx = pick_w([&](int w) { return smem_xpass<double>(L, w); });
+        const int wx = pick_xpass_w<double>(L);
         const int wz = pick_w([&](int w) { return smem_zpass<double>(L, w); });
         if (!wx || !wz) return 0;
         return smem_xpass<double>(L, wx);
     }
-    const int wx = pick_w([&](int w) { return smem_xpass<float>(L, w); });
+    const int wx = pick_xpass_w<float>(L);
     return wx ? smem_xpass<float>(L, wx) : 0;
 }
 

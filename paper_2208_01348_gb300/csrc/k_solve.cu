@@ -77,22 +77,34 @@ __global__ void k_dot(int n3, int nblk, const cx<Rl>* __restrict__ a, const cx<R
     }
 }
 
-__device__ __forceinline__ void sum_parts(const double* part, int s, int nblk, double (&o)[4]) {
-    o[0] = o[1] = o[2] = o[3] = 0.0;
-    const double* p = part + (size_t)s * nblk * 4;
-    for (int b = 0; b < nblk; ++b) {
-        o[0] += p[4 * b]; o[1] += p[4 * b + 1]; o[2] += p[4 * b + 2]; o[3] += p[4 * b + 3];
+// Sums part[s][b][0..3] over the blocks b < nblk: lane l adds blocks l, l+32,
+// ... in order, then a fixed shuffle tree adds the lanes.  Called by all 32
+// lanes of a warp; every lane receives the sums.  The order depends only on
+// nblk, so a system's result does not depend on the other systems.
+__device__ __forceinline__ void warp_sum_parts(const double* part, int s, int nblk, double (&o)[4]) {
+    const int lane = threadIdx.x & 31;
+    const double2* p = reinterpret_cast<const double2*>(part + (size_t)s * nblk * 4);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (int b = lane; b < nblk; b += 32) {
+        const double2 u = p[2 * b], v = p[2 * b + 1];
+        a0 += u.x; a1 += u.y; a2 += v.x; a3 += v.y;
     }
+    o[0] = warp_sum(a0); o[1] = warp_sum(a1); o[2] = warp_sum(a2); o[3] = warp_sum(a3);
 }
+
+// Warp-per-system kernels: 4 systems per 128-thread block.
+__device__ __forceinline__ int warp_system() { return blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); }
+static inline unsigned warp_blocks(int S) { return (unsigned)((S + 3) / 4); }
 
 // ------------------------------------------------------------------- QMR
 template <typename Rl>
 __global__ void k_qmr_start(KrylovArgs<Rl> k) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = warp_system();
     if (s >= k.S) return;
     if (!k.active[s]) return;
     double o[4];
-    sum_parts(k.part_a, s, k.nblk, o);     // (b.b, |b|^2)
+    warp_sum_parts(k.part_a, s, k.nblk, o);     // (b.b, |b|^2)
+    if (threadIdx.x & 31) return;
     QmrState q;
     const double rho = sqrt(o[2]);
     q.bnorm = rho;
@@ -141,12 +153,14 @@ __global__ void k_lanczos(KrylovArgs<Rl> k, int n) {
     const int s = blockIdx.y, blk = blockIdx.x;
     if (!k.active[s]) return;
     __shared__ double2 sc[2];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double o[4];
-        sum_parts(k.part_a, s, k.nblk_a, o);
-        const QmrState& q = k.qmr[s];
-        sc[0] = cdiv(make_double2(o[0], o[1]), q.delta);
-        sc[1] = q.beta;
+        warp_sum_parts(k.part_a, s, k.nblk_a, o);
+        if (threadIdx.x == 0) {
+            const QmrState& q = k.qmr[s];
+            sc[0] = cdiv(make_double2(o[0], o[1]), q.delta);
+            sc[1] = q.beta;
+        }
     }
     __syncthreads();
     const cx<Rl> al = cvt<cx<Rl>>(sc[0]), be = cvt<cx<Rl>>(sc[1]);
@@ -171,13 +185,18 @@ __global__ void k_lanczos(KrylovArgs<Rl> k, int n) {
 
 template <typename Rl>
 __global__ void k_qmr_step(KrylovArgs<Rl> k) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = warp_system();
     if (s >= k.S) return;
-    if (!k.active[s]) { k.upd[s] = 0; return; }
-    QmrState q = k.qmr[s];
+    const bool lead = (threadIdx.x & 31) == 0;
+    if (!k.active[s]) {
+        if (lead) k.upd[s] = 0;
+        return;
+    }
     double oa[4], ob[4];
-    sum_parts(k.part_a, s, k.nblk_a, oa);
-    sum_parts(k.part_b, s, k.nblk, ob);
+    warp_sum_parts(k.part_a, s, k.nblk_a, oa);
+    warp_sum_parts(k.part_b, s, k.nblk, ob);
+    if (!lead) return;
+    QmrState q = k.qmr[s];
     const double2 alpha = cdiv(make_double2(oa[0], oa[1]), q.delta);
     const double rho_n = sqrt(ob[2]);
     // Givens: apply rotations n-2, n-1 to the column (beta_n, alpha_n, rho_{n+1})
@@ -260,7 +279,7 @@ void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
     count_launch();
     k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.V[1], k.V[1], k.part_a, k.active);
     count_launch();
-    k_qmr_start<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    k_qmr_start<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
     count_launch();
     k_qmr_scale<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
 }
@@ -274,7 +293,7 @@ void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, bool dot_done, cudaS
     count_launch();
     k_lanczos<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k, n);
     count_launch();
-    k_qmr_step<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    k_qmr_step<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
     count_launch();
     k_qmr_update<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k, n);
 }
@@ -332,10 +351,11 @@ __global__ void k_bicg_copy(KrylovArgs<Rl> k) {
 
 template <typename Rl>
 __global__ void k_bicg_start(KrylovArgs<Rl> k) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = warp_system();
     if (s >= k.S || !k.active[s]) return;
     double o[4];
-    sum_parts(k.part_a, s, k.nblk, o);     // (r.r, |r|^2)
+    warp_sum_parts(k.part_a, s, k.nblk, o);     // (r.r, |r|^2)
+    if (threadIdx.x & 31) return;
     BicgState b;
     b.rho = make_double2(o[0], o[1]);
     b.bnorm = sqrt(o[2]);
@@ -358,12 +378,14 @@ __global__ void k_bicg_s(KrylovArgs<Rl> k) {
     const int s = blockIdx.y;
     if (!k.active[s]) return;
     __shared__ double2 al;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double o[4];
-        sum_parts(k.part_a, s, k.nblk, o);
-        const double2 rv = make_double2(o[0], o[1]);
-        al = (abs2_(rv) > 0.0) ? cdiv(k.bicg[s].rho, rv) : make_double2(0, 0);
-        if (blockIdx.x == 0) k.bicg[s].alpha = al;
+        warp_sum_parts(k.part_a, s, k.nblk, o);
+        if (threadIdx.x == 0) {
+            const double2 rv = make_double2(o[0], o[1]);
+            al = (abs2_(rv) > 0.0) ? cdiv(k.bicg[s].rho, rv) : make_double2(0, 0);
+            if (blockIdx.x == 0) k.bicg[s].alpha = al;
+        }
     }
     __syncthreads();
     const cx<Rl> a = cvt<cx<Rl>>(al);
@@ -378,12 +400,14 @@ __global__ void k_bicg_x(KrylovArgs<Rl> k) {
     const int s = blockIdx.y, blk = blockIdx.x;
     if (!k.active[s]) return;
     __shared__ double2 sc[2];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double o[4];
-        sum_parts(k.part_b, s, k.nblk, o);
-        sc[0] = k.bicg[s].alpha;
-        sc[1] = o[2] > 0.0 ? make_double2(o[0] / o[2], o[1] / o[2]) : make_double2(0, 0);
-        if (blk == 0) k.bicg[s].omega = sc[1];
+        warp_sum_parts(k.part_b, s, k.nblk, o);
+        if (threadIdx.x == 0) {
+            sc[0] = k.bicg[s].alpha;
+            sc[1] = o[2] > 0.0 ? make_double2(o[0] / o[2], o[1] / o[2]) : make_double2(0, 0);
+            if (blk == 0) k.bicg[s].omega = sc[1];
+        }
     }
     __syncthreads();
     const cx<Rl> al = cvt<cx<Rl>>(sc[0]), om = cvt<cx<Rl>>(sc[1]);
@@ -409,12 +433,17 @@ __global__ void k_bicg_x(KrylovArgs<Rl> k) {
 
 template <typename Rl>
 __global__ void k_bicg_step(KrylovArgs<Rl> k) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = warp_system();
     if (s >= k.S) return;
-    if (!k.active[s]) { k.upd[s] = 0; return; }
-    BicgState b = k.bicg[s];
+    const bool lead = (threadIdx.x & 31) == 0;
+    if (!k.active[s]) {
+        if (lead) k.upd[s] = 0;
+        return;
+    }
     double o[4];
-    sum_parts(k.part_a, s, k.nblk, o);
+    warp_sum_parts(k.part_a, s, k.nblk, o);
+    if (!lead) return;
+    BicgState b = k.bicg[s];
     const double2 rho_n = make_double2(o[0], o[1]);
     b.res = sqrt(o[2]) / b.bnorm;
     b.iters += 1;
@@ -453,7 +482,7 @@ void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
     count_launch();
     k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.R, k.R, k.part_a, k.active);
     count_launch();
-    k_bicg_start<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    k_bicg_start<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
 }
 
 template <typename Rl>
@@ -471,7 +500,7 @@ void launch_bicg_stage2(const KrylovArgs<Rl>& k, cudaStream_t st) {
     count_launch();
     k_bicg_x<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k);
     count_launch();
-    k_bicg_step<Rl><<<(k.S + 127) / 128, 128, 0, st>>>(k);
+    k_bicg_step<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
     count_launch();
     k_bicg_p<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
 }
@@ -515,10 +544,11 @@ __global__ void k_norms2(int n3, int nblk, const double2* a, const double2* b, d
 
 __global__ void k_residual_check(int S, int nblk, const double* part, double eps, double eps_floor, double safety,
                                  double* res, double* rnorm, int* outer, int* n_outer, double* eps_sys) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = warp_system();
     if (s >= S) return;
     double o[4];
-    sum_parts(part, s, nblk, o);
+    warp_sum_parts(part, s, nblk, o);
+    if (threadIdx.x & 31) return;
     const double rn = sqrt(o[0]), bn = sqrt(o[1]);
     const double r = bn > 0 ? rn / bn : 0.0;
     res[s] = r;
@@ -577,7 +607,7 @@ void launch_residual_check(int S, int nblk, const double* part, double eps, doub
                            double* res, double* rnorm, int* outer, int* n_outer, double* eps_sys, cudaStream_t st) {
     cudaMemsetAsync(n_outer, 0, sizeof(int), st);
     count_launch();
-    k_residual_check<<<(S + 127) / 128, 128, 0, st>>>(S, nblk, part, eps, eps_floor, safety, res, rnorm, outer, n_outer,
+    k_residual_check<<<warp_blocks(S), 128, 0, st>>>(S, nblk, part, eps, eps_floor, safety, res, rnorm, outer, n_outer,
                                                       eps_sys);
 }
 template <typename Rl>

@@ -253,3 +253,4 @@ def test_async_solve_matches_blocking_solve(dd, ctx):
     res = job.wait()
     for a, b in ((res.p_eels, ref.p_eels), (res.p_cl, ref.p_cl), (res.p_ext, ref.p_ext), (res.p, ref.p)):
         assert np.array_equal(a, b)
+
