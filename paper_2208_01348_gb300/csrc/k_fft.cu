@@ -449,6 +449,176 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
 }
 
 // ---------------------------------------------------------------------------
+// Fused slab passes for My = Mz = 64 in FP32, register resident.
+//
+// A warp transforms 4 lines at once: lane = q + 4p holds, for its line q, the
+// elements p + 8r (r = 0..7) of the 64-point line.  A length-8 DFT over the
+// lane's registers, the twiddles exp(-+2 pi i p k / 64), a transpose among the
+// 8 lanes of the line (through a warp-private shared tile) and a second
+// length-8 DFT leave element j + 8k of the transform in register k of lane
+// j: input and output use the same (lane, register) <-> index map, forward
+// and inverse alike.  Between the y and the z transforms the slab
+// S[64][Nz] sits in shared memory (row stride 36 = 4 mod 16: the 4 x 4
+// (line, lane) patterns of every access hit distinct banks); the block
+// synchronises once per pass.
+// ---------------------------------------------------------------------------
+constexpr int R64_QS = 132;   // transpose tile strides (8-byte units): line -> 4, lane -> 1 (mod 16)
+constexpr int R64_PS = 17;
+constexpr int R64_TILE = 4 * R64_QS;
+constexpr int R64_SLS = 36;   // slab row stride
+
+template <bool INV>
+__device__ __forceinline__ void fft64_warp(float2 (&v)[8], float2* tile, int q, int p, const float2* tw) {
+    Dft<8, INV, float2>::run(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        float2 w = tw[p * k];
+        if (INV) w.y = -w.y;
+        v[k] = v[k] * w;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tile[q * R64_QS + p * R64_PS + k] = v[k];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = tile[q * R64_QS + i * R64_PS + p];
+    __syncwarp();
+    Dft<8, INV, float2>::run(v);
+}
+
+struct Slab64Smem {
+    float2 tw[64];
+    float2 S[64 * R64_SLS];
+    float2 tile[FFT_THREADS / 32][R64_TILE];
+};
+
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, MatvecArgs<float> a) {
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Slab64Smem& sm = *reinterpret_cast<Slab64Smem*>(smem_raw);
+    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
+    const int nwarp = blockDim.x >> 5;
+    const float2* twg = tw_of<float>(L, 1);          // My = Mz = 64: the y and z tables coincide
+    if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
+    __syncthreads();
+    float2* tile = sm.tile[warp];
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
+    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    const C zero = make_float2(0.f, 0.f);
+    // y transforms of the Nz columns, 4 per warp: gathered from x, into S
+    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
+        const int iz = iz0 + q;
+        C v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = p + 8 * r;
+            v[r] = zero;
+            if (y < Ny && iz < Nz) {
+                const int dip = cm[y * Nz + iz];
+                if (dip >= 0) v[r] = xs[dip] * to_f(cf[L.mat[dip]]);
+            }
+        }
+        fft64_warp<false>(v, tile, q, p, sm.tw);
+        if (iz < Nz) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sm.S[(p + 8 * k) * R64_SLS + iz] = v[k];
+        }
+    }
+    __syncthreads();
+    // z transforms of the 64 rows, 4 per warp: from S, written to U
+    C* U = a.U + (((size_t)s * 3 + c) * 64 * L.Nx + ix) * 64;
+    const size_t row = (size_t)L.Nx * 64;
+    for (int ky0 = warp * 4; ky0 < 64; ky0 += nwarp * 4) {
+        const int ky = ky0 + q;
+        C v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int z = p + 8 * r;
+            v[r] = z < Nz ? sm.S[ky * R64_SLS + z] : zero;
+        }
+        fft64_warp<false>(v, tile, q, p, sm.tw);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) U[(size_t)ky * row + p + 8 * k] = v[k];
+    }
+}
+
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, MatvecArgs<float> a, float invM) {
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Slab64Smem& sm = *reinterpret_cast<Slab64Smem*>(smem_raw);
+    __shared__ float red[2 * FFT_THREADS / 32];
+    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
+    const int nwarp = blockDim.x >> 5;
+    const float2* twg = tw_of<float>(L, 2);
+    if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
+    __syncthreads();
+    float2* tile = sm.tile[warp];
+    // inverse z transforms of the 64 rows of U, first Nz outputs into S
+    const C* U = a.U + (((size_t)s * 3 + c) * 64 * L.Nx + ix) * 64;
+    const size_t row = (size_t)L.Nx * 64;
+    for (int ky0 = warp * 4; ky0 < 64; ky0 += nwarp * 4) {
+        const int ky = ky0 + q;
+        C v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = U[(size_t)ky * row + p + 8 * r];
+        fft64_warp<true>(v, tile, q, p, sm.tw);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int z = p + 8 * k;
+            if (z < Nz) sm.S[ky * R64_SLS + z] = v[k];
+        }
+    }
+    __syncthreads();
+    // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    C* ys = a.y + ((size_t)s * 3 + c) * L.N;
+    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
+    const double2* dg = a.diag + (size_t)s * EELS_MAX_MAT;
+    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    float dot0 = 0.f, dot1 = 0.f;
+    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
+        const int iz = iz0 + q;
+        C v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = iz < Nz ? sm.S[(p + 8 * r) * R64_SLS + iz] : make_float2(0.f, 0.f);
+        fft64_warp<true>(v, tile, q, p, sm.tw);
+        if (iz >= Nz) continue;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int y = p + 8 * k;
+            if (y >= Ny) continue;
+            const int dip = cm[y * Nz + iz];
+            if (dip < 0) continue;
+            const int m = L.mat[dip];
+            const C xv = xs[dip];
+            const C yv = to_f(dg[m]) * xv - to_f(cf[m]) * (invM * v[k]);
+            ys[dip] = yv;
+            dot0 += xv.x * yv.x - xv.y * yv.y;
+            dot1 += xv.x * yv.y + xv.y * yv.x;
+        }
+    }
+    if (a.dot_part) {
+        // block sum in a fixed order (warp shuffles, then thread 0 over the warps)
+        for (int o = 16; o > 0; o >>= 1) {
+            dot0 += __shfl_xor_sync(0xffffffffu, dot0, o);
+            dot1 += __shfl_xor_sync(0xffffffffu, dot1, o);
+        }
+        if (lane == 0) { red[2 * warp] = dot0; red[2 * warp + 1] = dot1; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0, s1 = 0;
+            for (int i = 0; i < nwarp; ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
+            double* pp = a.dot_part + (((size_t)s * 3 + c) * L.Nx + ix) * 4;
+            pp[0] = s0; pp[1] = s1; pp[2] = 0.0; pp[3] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static const size_t kSmemCap = 220 * 1024;
@@ -539,8 +709,21 @@ static void slab_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, 
     else k_slab_inv<Rl, CW><<<grid, FFT_THREADS, sm, st>>>(L, a, (Rl)(1.0 / ((double)L.Mx * L.My * L.Mz)));
 }
 
+// Register-resident slab kernels: FP32 with 64-point y and z transforms.
+template <typename Rl> static bool slab64_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st);
+template <> bool slab64_launch<double>(const LatticeDev&, const MatvecArgs<double>&, bool, cudaStream_t) { return false; }
+template <> bool slab64_launch<float>(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
+    if (L.My != 64 || L.Mz != 64) return false;
+    dim3 grid(L.Nx, a.S * 3);
+    count_launch();
+    if (!inv) k_slab_fwd64<<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a);
+    else k_slab_inv64<<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a, (float)(1.0 / ((double)L.Mx * L.My * L.Mz)));
+    return true;
+}
+
 template <typename Rl> static void slab_launch_any(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, int cw,
                                                    cudaStream_t st) {
+    if (slab64_launch<Rl>(L, a, inv, st)) return;
     if (cw == 32) slab_launch<Rl, 32>(L, a, inv, st);
     else if (cw == 16) slab_launch<Rl, 16>(L, a, inv, st);
     else slab_launch<Rl, 8>(L, a, inv, st);
@@ -600,6 +783,8 @@ void prepare_far_kernels();
 void prepare_kernels() {
     prepare_w<float, 8>(); prepare_w<float, 16>(); prepare_w<float, 32>();
     prepare_w<double, 8>(); prepare_w<double, 16>(); prepare_w<double, 32>();
+    allow_smem(k_slab_fwd64);
+    allow_smem(k_slab_inv64);
     prepare_far_kernels();
 }
 

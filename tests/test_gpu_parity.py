@@ -101,6 +101,29 @@ def test_matvec_equals_dense_oracle(dd, ctx, dims):
         assert rel(y32[i], ref[i]) < 2e-5
 
 
+@pytest.mark.parametrize("dims", [(4, 32, 31), (3, 31, 32), (6, 32, 32)])
+def test_matvec_64_point_transforms_equal_fft_oracle(dd, ctx, dims):
+    """Lattices whose y and z transforms are 64 points long (the FP32 path
+    then uses the register-resident slab kernels); the oracle is its own
+    FFT convolution (period 2N), itself pinned to the dense matrix."""
+    nx, ny, nz = dims
+    occ = _random_grid(dims, seed=7 * nx + ny + nz, nmat=2)
+    d_nm = 1.5
+    dd.eels_set_grid(ctx, occ, d_nm)
+    assert dd.eels_padded_dims(ctx)[1:] == (64, 64)
+    eps_p = [I.drude(2.0), 2.5 + 0.3j]
+    eps_h = 2.1025 + 0j
+    pt = run.setup(nx, ny, nz, d_nm, occ, 2.0, eps_p, eps_h, (100.0, 100.0), ekin_keV=120.0)
+    op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha)
+    x = I.random_complex((2, len(pt.r), 3), seed=11)
+    ref = np.stack([op.matvec(xi) for xi in x])
+    y32 = dd.eels_apply_matrix(ctx, dd.EELS_MIXED, 2.0, eps_p, eps_h, x)
+    y64 = dd.eels_apply_matrix(ctx, dd.EELS_FP64, 2.0, eps_p, eps_h, x)
+    for i in range(2):
+        assert rel(y64[i], ref[i]) < 1e-12
+        assert rel(y32[i], ref[i]) < 2e-5
+
+
 # ------------------------------------------------------------------ solve
 def _solve(dd, ctx, w, precision, energies=None, beams=None, n_dir=2562, want_p=True, eps=1e-10, max_batch=0):
     g = w.grid
