@@ -301,6 +301,8 @@ def main():
     ap.add_argument("--serve-concurrency", type=int, default=8)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-sample", type=int, default=5,
+                    help="energies of the plain FP64 single-system comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--matvec-reps", type=int, default=20)
     args = ap.parse_args()
@@ -413,6 +415,26 @@ def main():
     traffic = None
     if TRAFFIC_BYTES_PER_SYSTEM is not None and TRAFFIC_SRC_HASH == kernel_src_hash():
         traffic = TRAFFIC_BYTES_PER_SYSTEM * S
+
+    # the plain FP64 path, one system per solve, on a sample of the energies
+    # (first beam): its points/s, and how far the mixed results are from it
+    fp64_cmp = None
+    if prec == dd.EELS_MIXED and world == 1 and args.fp64_sample > 0:
+        idx = np.unique(np.linspace(0, len(w.energies_eV) - 1, args.fp64_sample).round().astype(int))
+        o64 = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=dd.EELS_FP64, eps_it=1e-8, n_dir=w.n_dir,
+                                   max_batch=1)
+        dd.eels_set_grid(ctx, g.occ, g.d_nm)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64 = dd.eels_solve(ctx, o64, w.energies_eV[idx], w.eps_p[idx], w.eps_h[idx], w.beams_nm[:1], want_cl=True)
+        torch.cuda.synchronize()
+        v64 = len(idx) / (time.perf_counter() - t0)
+        rel_e = np.abs(res.p_eels[idx, 0] - r64.p_eels[:, 0]) / np.abs(r64.p_eels[:, 0])
+        rel_c = np.abs(res.p_cl[idx, 0] - r64.p_cl[:, 0]) / np.abs(r64.p_cl[:, 0])
+        fp64_cmp = {"value": v64, "unit": "points/s",
+                    "sample": f"energies {idx.tolist()} of {w.name}, beam 0, one system per solve, eps 1e-8",
+                    "mixed_over_fp64": value / v64, "p_eels_max_rel_diff": float(rel_e.max()),
+                    "p_cl_max_rel_diff": float(rel_c.max())}
     dd.eels_destroy(ctx)
 
     if rank != 0:
@@ -435,6 +457,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if fp64_cmp:
+        out["fp64_single_rhs"] = fp64_cmp
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, w)
     print(json.dumps(out))

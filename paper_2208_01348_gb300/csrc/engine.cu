@@ -636,21 +636,31 @@ int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::v
 
 // FP64 refinement of a batch.  EELS_MIXED: FP32 inner solves (restarted
 // every inner_max_iter iterations) until every system reaches eps_it or
-// stalls (see refine_rounds) or 30 rounds pass; systems still above eps_it
-// then continue with FP64 inner solves.  Lattices whose padded FFT
-// grid is below 16^3 points go straight to FP64 inner solves: their matvec is
-// bound by launch latency, so FP32 would save nothing and cost iterations.
-// EELS_FP64: FP64 inner solves.
+// stalls (see refine_rounds) or 30 rounds pass.  With QMR, the systems left
+// then continue with FP32 BiCGStab: the complex-symmetric Lanczos process of
+// QMR can stall or break down on a residual whose unconjugated square r^T r
+// is small, where BiCGStab, with its conjugated inner product, does not.
+// Systems still above eps_it finish with FP64 inner solves (BiCGStab after
+// FP32 rounds, for the same reason).  Lattices whose padded FFT grid is
+// below 16^3 points go straight to FP64 inner solves with the chosen solver:
+// their matvec is bound by launch latency, so FP32 would save nothing and
+// cost iterations.  EELS_FP64: FP64 inner solves with the chosen solver.
 void refine_batch(eels_ctx* c, int S, const eels_opts* o, bool fp64, std::vector<int>& iters, std::vector<int>& refin,
                   std::vector<double>& resid) {
     cudaStream_t st = c->stream;
     int left = 1;
     const size_t m_pad = (size_t)c->L.Mx * c->L.My * c->L.Mz;
-    if (!fp64 && m_pad >= (size_t)16 * 16 * 16) left = refine_rounds<float>(c, S, o, 30, iters, refin);
+    const bool fp32_rounds = !fp64 && m_pad >= (size_t)16 * 16 * 16;
+    eels_opts ob = *o;
+    ob.solver = EELS_BICGSTAB;
+    if (fp32_rounds) {
+        left = refine_rounds<float>(c, S, o, 30, iters, refin);
+        if (left > 0 && o->solver == EELS_QMR) left = refine_rounds<float>(c, S, &ob, 30, iters, refin);
+    }
     if (left > 0) {
         const size_t kvec64 = (size_t)S * 3 * c->N * sizeof(double2);
         for (auto& b : c->kv) b.ensure(kvec64);
-        refine_rounds<double>(c, S, o, 8, iters, refin);
+        refine_rounds<double>(c, S, fp32_rounds ? &ob : o, 8, iters, refin);
     }
     CK(cudaMemcpyAsync(resid.data(), c->res.p, S * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

@@ -304,13 +304,14 @@ template void launch_qmr_post_matvec<float>(const KrylovArgs<float>&, int, bool,
 template void launch_qmr_post_matvec<double>(const KrylovArgs<double>&, int, bool, cudaStream_t);
 
 // ------------------------------------------------------------- BiCGStab
-// van der Vorst (SIAM J. Sci. Stat. Comput. 13 (1992) 631) with the shadow
-// residual r^ = r0 and the unconjugated form r^T y for rho and alpha (the
-// complex-symmetric variant); omega minimises ||s - omega t|| with the
-// conjugated inner product.  Per iteration:
-//   v = A p, alpha = rho / r^T v, s = r - alpha v, t = A s,
+// van der Vorst (SIAM J. Sci. Stat. Comput. 13 (1992) 631) for a general
+// complex matrix: shadow residual r^ = r0 and the conjugated inner product
+// throughout, so rho_0 = ||r0||^2 > 0 and the method cannot break down at the
+// start on a residual whose unconjugated square r^T r is near zero (where
+// the complex-symmetric Lanczos process of QMR does).  Per iteration:
+//   v = A p, alpha = rho / r^^H v, s = r - alpha v, t = A s,
 //   omega = (t^H s) / (t^H t), x += alpha p + omega s, r = s - omega t,
-//   rho' = r^T r, beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
+//   rho' = r^^H r, beta = (rho'/rho)(alpha/omega), p = r + beta (p - omega v).
 
 // part[s][blk] = (Re sum conj(a) b, Im, sum |a|^2, 0)
 template <typename Rl>
@@ -354,7 +355,7 @@ __global__ void k_bicg_start(KrylovArgs<Rl> k) {
     const int s = warp_system();
     if (s >= k.S || !k.active[s]) return;
     double o[4];
-    warp_sum_parts(k.part_a, s, k.nblk, o);     // (r.r, |r|^2)
+    warp_sum_parts(k.part_a, s, k.nblk, o);     // (r^H r, |r|^2)
     if (threadIdx.x & 31) return;
     BicgState b;
     b.rho = make_double2(o[0], o[1]);
@@ -420,8 +421,8 @@ __global__ void k_bicg_x(KrylovArgs<Rl> k) {
         const cx<Rl> r = sv - om * k.Tb[off + i];
         k.R[off + i] = r;
         const cx<Rl> h = k.Rh[off + i];
-        acc[0] += h.x * r.x - h.y * r.y;
-        acc[1] += h.x * r.y + h.y * r.x;
+        acc[0] += h.x * r.x + h.y * r.y;      // conj(r^) . r
+        acc[1] += h.x * r.y - h.y * r.x;
         acc[2] += r.x * r.x + r.y * r.y;
     }
     block_sum<Rl, 4>(acc);
@@ -480,7 +481,7 @@ void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
     count_launch();
     k_bicg_copy<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
     count_launch();
-    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.R, k.R, k.part_a, k.active);
+    k_dotc<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.R, k.R, k.part_a, k.active);
     count_launch();
     k_bicg_start<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
 }
@@ -488,7 +489,7 @@ void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
 template <typename Rl>
 void launch_bicg_stage1(const KrylovArgs<Rl>& k, cudaStream_t st) {
     count_launch();
-    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.Rh, k.Vb, k.part_a, k.active);
+    k_dotc<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.Rh, k.Vb, k.part_a, k.active);
     count_launch();
     k_bicg_s<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
 }

@@ -57,8 +57,8 @@ constexpr int RED_CHUNK = 4096;    // vector entries per reduction block
 template <typename Rl> void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_t st);
 // One QMR iteration n >= 1; the caller supplies the matvec (W = A V[n%2]).
 template <typename Rl> void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, bool dot_done, cudaStream_t st);
-// BiCGStab (van der Vorst 1992) with the unconjugated shadow residual
-// r^ = r0 (complex-symmetric form); rhs in R, X = 0.
+// BiCGStab (van der Vorst 1992) with the shadow residual r^ = r0 and the
+// conjugated inner product (general complex form); rhs in R, X = 0.
 // Vector roles: R (residual; the rhs on entry, S = R - alpha V overwrites
 // it), Rh (shadow), Pb (direction), Vb = A Pb, Tb = A S, X (iterate).
 template <typename Rl> void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream_t st);
