@@ -300,6 +300,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-concurrency", type=int, default=8)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--solver", default="qmr", choices=["qmr", "bicgstab"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=5,
                     help="energies of the plain FP64 single-system comparison (0: skip)")
@@ -345,7 +346,8 @@ def main():
     ctx = dd.eels_create(local, stream.cuda_stream)
     g = w.grid
     prec = dd.EELS_MIXED if args.precision == "mixed" else dd.EELS_FP64
-    opts = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=prec, eps_it=1e-8, eps_inner=1e-5, n_dir=w.n_dir)
+    opts = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=prec, eps_it=1e-8, eps_inner=1e-5, n_dir=w.n_dir,
+                                solver=dd.EELS_QMR if args.solver == "qmr" else dd.EELS_BICGSTAB)
     dd.eels_set_grid(ctx, g.occ, g.d_nm)
 
     def step():
@@ -445,7 +447,7 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64" if prec == dd.EELS_MIXED else "f64",
         "data": "synthetic (Drude permittivities stand in for tabulated optical data)",
         "config": {"workload": w.name, "points_per_gpu": w.n_points, "dipoles": n, "fft": [mx, my, mz],
-                   "precision": args.precision, "eps_it": 1e-8, "eps_inner": 1e-5, "n_dir": w.n_dir,
+                   "precision": args.precision, "solver": args.solver, "eps_it": 1e-8, "eps_inner": 1e-5, "n_dir": w.n_dir,
                    "l2": "working set of a step > L2 (several GB of per-system vectors)",
                    "iters_mean": float(np.mean(res.iters)), "residual_max": float(np.max(res.residual))},
         "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
