@@ -210,11 +210,10 @@ long long eels_kernel_launches(void);
  * The same matrix-vector product for callers that cannot allocate device
  * memory.  The paper has no counterpart; this is a library-integration
  * entry point.  Callers that cannot let a library allocate at the time of
- * the call include code that runs while a stream is being captured into a
- * CUDA graph (the allocator may not be called there), real-time or
- * latency-critical loops that must not meet the allocator's implicit
- * synchronisation, and hosts that own all device memory through their own
- * pool.  eels_matvec_dev_noalloc applies the operator prepared by
+ * the call include real-time or latency-critical loops that must not meet
+ * the allocator's implicit synchronisation, and hosts (plugins inside a
+ * larger application, frameworks with their own caching pool) that own all
+ * device memory and forbid foreign allocations.  eels_matvec_dev_noalloc applies the operator prepared by
  * eels_prepare_operator with the same kernels as eels_matvec_dev, but takes
  * its FFT scratch from one fixed array compiled into the library
  * (EELS_NOALLOC_SCRATCH_BYTES = 64 MiB of device memory, held by every GPU

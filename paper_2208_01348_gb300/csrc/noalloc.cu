@@ -2,11 +2,10 @@
 //
 // eels_matvec_dev keeps its FFT scratch in the context, which grows it with
 // the device allocator on demand.  Some callers cannot let a library call
-// the allocator at that point: code that runs while a stream is being
-// captured into a CUDA graph (allocation calls are not allowed there),
-// real-time or latency-critical loops that must not hit the allocator's
-// implicit synchronisation, and hosts that own all device memory through
-// their own pool and forbid foreign allocations.  eels_matvec_dev_noalloc
+// the allocator at that point: real-time or latency-critical loops that
+// must not hit the allocator's implicit synchronisation, and hosts (plugins
+// inside a larger application, frameworks with their own caching pool) that
+// own all device memory and forbid foreign allocations.  eels_matvec_dev_noalloc
 // applies the same prepared operator with the same kernels, but its FFT
 // scratch is one fixed array compiled into the library: a file-scope
 // __device__ array of EELS_NOALLOC_SCRATCH_BYTES (64 MiB) that every GPU which

@@ -1,8 +1,7 @@
 """eels_matvec_dev_noalloc: the FFT matrix-vector product for callers that
-cannot allocate device memory (for example code running while a stream is
-captured into a CUDA graph, latency-critical loops that must not meet the
-allocator's synchronisation, or hosts whose memory pool owns the whole
-device).  Its FFT scratch is a fixed 64 MiB array inside the library.
+cannot allocate device memory (for example latency-critical loops that must
+not meet the allocator's synchronisation, or hosts whose own memory pool owns
+the whole device).  Its FFT scratch is a fixed 64 MiB array inside the library.
 
 Checked through the C ABI against eels_matvec_dev (context-owned scratch),
 with the tolerances the matvec parity tests use, on two calls in a row (the
