@@ -284,6 +284,21 @@ int eels_server_stats(eels_server* s, int* running_max, int* completed, size_t* 
 /* Finish running requests, drop queued ones, join the workers. */
 void eels_server_destroy(eels_server* s);
 
+/* Particle-related total light-emission probability P_CL^tot (Eq. 41, in
+ * its second form C_enh - C_ext + C_sca): out[i] = p_eels[i] - p_ext[i] +
+ * p_cl[i] for i < n, eV^-1, host arrays (out may alias an input).  It is
+ * meaningful in a non-absorbing host (Sec. 2.6) and equals p_cl below the
+ * Cherenkov threshold.  EELS_E_INVALID_ARG for n < 0 or NULL arrays. */
+int eels_cl_total(int n, const double* p_eels, const double* p_ext, const double* p_cl, double* out);
+
+/* Loss of the electron to the host alone (no particle) per unit path
+ * length, as a probability density in eV^-1 m^-1: Eq. 29 (Frank-Tamm) with
+ * the (2/pi)/(hbar^2 w) of Eq. 37; it does not depend on the loss energy for
+ * a host with constant eps_h, and is 0 at and below the Cherenkov threshold
+ * (Eq. 28).  eps_h must be real and positive (W0 diverges in an absorbing
+ * host, Sec. 2.5): EELS_E_INVALID_ARG otherwise. */
+int eels_frank_tamm(double ekin_keV, eels_c128 eps_h, double* dp_dz);
+
 /* The far-field direction grid the CL reduction uses (icosphere with
  * n_dir = 10*4^L+2 vertices): dirs [n_dir][3] unit vectors, weights
  * [n_dir] (sum 4 pi).  Host outputs. */

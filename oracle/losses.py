@@ -74,3 +74,26 @@ def p_sca_img(r, p_t, k, eps_h, omega):
     q = np.einsum("ia,ijab,jb->", np.conj(p_t), ImG, p_t)
     W = (omega / 2.0) * 4.0 * np.pi * EPS0 * np.real(eps_h) * np.real(q)
     return _to_prob(W, omega)
+
+
+def p_cl_tot(P_EELS, P_ext, P_CL):
+    """Particle-related total emission probability P_CL^tot (Eq. 41), in its
+    second form: the prefactor of Eq. 37 and 42 times (C_enh - C_ext + C_sca),
+    i.e. P_EELS - P_ext + P_CL.  Meaningful in a non-absorbing host (Sec. 2.6);
+    it equals P_CL below the Cherenkov threshold, where P_EELS = P_ext."""
+    return P_EELS - P_ext + P_CL
+
+
+def frank_tamm_rate(v: float, m_h: float) -> float:
+    """Free-space (particle-free) loss of the electron per unit path length,
+    as a probability density in eV^-1 m^-1: Eq. 29 for dW0/dz, turned into a
+    probability by the (2/pi) / (hbar^2 w) of Eq. 37, times e.  The omega of
+    Eq. 29 cancels: (mu0 q^2 / (4 pi hbar^2)) (1 - c^2 / (v^2 m_h^2)).  Zero at
+    and below the threshold beta_h = v m_h / c <= 1 (Eq. 28).  Real host
+    index only (W0 diverges in an absorbing host, Sec. 2.5)."""
+    from .constants import MU0, Q_ELECTRON
+    beta_h = v * m_h / C_LIGHT
+    if beta_h <= 1.0:
+        return 0.0
+    dW0_dz_over_w = MU0 / 8.0 * Q_ELECTRON ** 2 * (1.0 - 1.0 / beta_h ** 2)
+    return 2.0 / np.pi * dW0_dz_over_w / HBAR ** 2 * E_CHARGE

@@ -1177,6 +1177,21 @@ int eels_internal_matvec_with_scratch(eels_ctx* c, int precision, const void* x,
 
 extern "C" {
 
+int eels_cl_total(int n, const double* p_eels, const double* p_ext, const double* p_cl, double* out) {
+    if (n < 0 || (n > 0 && (!p_eels || !p_ext || !p_cl || !out))) return EELS_E_INVALID_ARG;
+    for (int i = 0; i < n; ++i) out[i] = p_eels[i] - p_ext[i] + p_cl[i];
+    return EELS_OK;
+}
+
+int eels_frank_tamm(double ekin_keV, eels_c128 eps_h, double* dp_dz) {
+    if (!dp_dz || !(ekin_keV > 0) || !(eps_h.re > 0) || eps_h.im != 0.0) return EELS_E_INVALID_ARG;
+    const double v = electron_speed(ekin_keV);
+    const double b2 = v * v * eps_h.re / (kC * kC);   // beta_h^2
+    // (2/pi) (dW0/dz) / (hbar^2 w) e with dW0/dz = (mu0/8) e^2 w (1 - 1/beta_h^2), mu0 = 1/(eps0 c^2)
+    *dp_dz = b2 <= 1.0 ? 0.0 : kE * kE * (1.0 - 1.0 / b2) / (4.0 * kPi * kEps0 * kC * kC * kHbar * kHbar) * kE;
+    return EELS_OK;
+}
+
 int eels_directions(int n_dir, double* dirs, double* weights) {
     std::vector<double> d, w;
     if (!dirs || !weights || !icosphere(n_dir, d, w)) return EELS_E_INVALID_ARG;

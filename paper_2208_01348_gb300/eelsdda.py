@@ -97,6 +97,8 @@ _sig = {
     "eels_prepare_operator": (C.c_int, [_P, C.c_int, _dp, C.c_int, _cp, _cp]),
     "eels_matvec_dev": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_kernel_launches": (C.c_longlong, []),
+    "eels_cl_total": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
+    "eels_frank_tamm": (C.c_int, [C.c_double, eels_c128, _dp]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
     "eels_server_submit": (C.c_int, [_P, C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp,
@@ -197,6 +199,13 @@ class SolveResult:
     residual: np.ndarray
     converged: np.ndarray
     code: int
+
+    @property
+    def p_cl_tot(self) -> Optional[np.ndarray]:
+        """P_CL^tot (Eq. 41) when P_ext and P_CL were requested."""
+        if self.p_ext is None or self.p_cl is None:
+            return None
+        return eels_cl_total(self.p_eels, self.p_ext, self.p_cl)
 
 
 class _SolveCall:
@@ -328,6 +337,21 @@ def eels_matvec_dev_noalloc(ctx, precision: int, x_ptr: int, y_ptr: int, n_sys: 
     stream capture)."""
     _check(_lib.eels_matvec_dev_noalloc(ctx, precision, _P(x_ptr), _P(y_ptr), n_sys, _P(stream) if stream else None),
            ctx)
+
+
+def eels_cl_total(p_eels, p_ext, p_cl) -> np.ndarray:
+    """P_CL^tot (Eq. 41) from the three probabilities (same shapes)."""
+    a, b, c = (np.ascontiguousarray(v, dtype=np.float64) for v in (p_eels, p_ext, p_cl))
+    out = np.empty_like(a)
+    _check(_lib.eels_cl_total(a.size, _dptr(a), _dptr(b), _dptr(c), _dptr(out)))
+    return out
+
+
+def eels_frank_tamm(ekin_keV: float, eps_h: complex) -> float:
+    """Host-only loss per unit path length, eV^-1 m^-1 (Eq. 29; 0 below threshold)."""
+    r = C.c_double()
+    _check(_lib.eels_frank_tamm(float(ekin_keV), eels_c128(complex(eps_h).real, complex(eps_h).imag), C.byref(r)))
+    return r.value
 
 
 def eels_kernel_launches() -> int:

@@ -84,3 +84,20 @@ def test_package_import_has_no_fallback():
         if f.endswith(".py"):
             src = open(os.path.join(pkg, f)).read()
             assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_host_utilities_eq29_eq41_match_oracle():
+    """Host-side utilities of the library (no GPU work): the Frank-Tamm loss
+    per unit length (Eq. 29) and P_CL^tot (Eq. 41) against the oracle."""
+    import numpy as np
+    from oracle import losses, physics
+    from paper_2208_01348_gb300 import eelsdda as dd
+    for ek, eps_h in ((200.0, 4.0), (100.0, 4.0), (100.0, 2.1025), (300.0, 2.25)):
+        ref = losses.frank_tamm_rate(physics.electron_speed(ek), np.sqrt(eps_h))
+        got = dd.eels_frank_tamm(ek, eps_h)
+        assert (got == 0.0 and ref == 0.0) or abs(got - ref) <= 1e-12 * abs(ref)
+    with pytest.raises(dd.EelsError):
+        dd.eels_frank_tamm(200.0, 4.0 + 0.05j)
+    rng = np.random.default_rng(3)
+    a, b, c = rng.random((3, 7, 2))
+    assert np.allclose(dd.eels_cl_total(a, b, c), losses.p_cl_tot(a, b, c), rtol=0, atol=1e-15)

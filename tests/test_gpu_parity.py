@@ -81,7 +81,8 @@ def _random_grid(dims, seed, frac=0.7, nmat=1):
     return occ
 
 
-@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (3, 4, 5), (7, 3, 2), (5, 9, 6), (12, 12, 12), (13, 6, 17)])
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (3, 4, 5), (7, 3, 2), (5, 9, 6), (12, 12, 12), (13, 6, 17),
+                                  (32, 5, 3), (31, 4, 6)])
 def test_matvec_equals_dense_oracle(dd, ctx, dims):
     nx, ny, nz = dims
     nmat = 2 if nx * ny * nz > 8 else 1
@@ -173,6 +174,8 @@ def test_reduced_spectrum_glass_host(dd, ctx, prec):
         _check_point(res, ie, 0, _oracle(w, ie, 0), tol, tol)
     # below the Cherenkov threshold the particle loss equals extinction (Sec. 2.4)
     assert np.allclose(res.p_eels, res.p_ext, rtol=1e-9 if prec == "FP64" else 1e-6, atol=0)
+    # ... so the total emission of Eq. 41 reduces to P_CL (Sec. 2.6)
+    assert np.all(np.abs(res.p_cl_tot - res.p_cl) <= (1e-9 if prec == "FP64" else 1e-6) * np.abs(res.p_eels))
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])

@@ -368,3 +368,34 @@ def test_small_sphere_eels_dipole_limit():
     E0 = field.incident_field(np.zeros((1, 3)), pt.omega, pt.v, pt.m_h, pt.gamma_h, b * NM, 0.0)[0]
     ref = 4 * EPS0 / HBAR ** 2 * np.imag(alpha) * np.sum(np.abs(E0) ** 2) * E_CHARGE
     assert o["P_EELS"] == pytest.approx(ref, rel=0.03)
+
+
+def test_frank_tamm_rate_equals_textbook_photon_count():
+    """Eq. 29 as a probability per unit length equals the Frank-Tamm photon
+    yield dN/(dx d(hbar w)) = (alpha / (hbar c)) (1 - 1/(beta^2 n^2)), written
+    with the measured fine-structure constant (CODATA 2018) instead of mu0,
+    and vanishes at and below the threshold (Eq. 28)."""
+    alpha_fs = 7.2973525693e-3
+    for ek, n in ((200.0, 2.0), (100.0, 2.0), (300.0, 1.5)):
+        v = physics.electron_speed(ek)
+        beta = v / C_LIGHT
+        ref = alpha_fs / (HBAR * C_LIGHT) * (1.0 - 1.0 / (beta * n) ** 2) * E_CHARGE
+        assert beta * n > 1
+        assert losses.frank_tamm_rate(v, n) == pytest.approx(ref, rel=1e-9)
+    v = physics.electron_speed(100.0)
+    n_thr = C_LIGHT / v
+    assert losses.frank_tamm_rate(v, 0.999 * n_thr) == 0.0
+    assert losses.frank_tamm_rate(v, n_thr * (1 + 1e-9)) < 1e-6 * losses.frank_tamm_rate(v, 2.0)
+
+
+def test_cl_total_forms_of_eq41_agree():
+    """P_CL^tot by its second form (C_enh - C_ext + C_sca) equals the first
+    form (C_enh - C_abs) with the exact Im-G scattering, in a real host below
+    and above the Cherenkov threshold, and equals P_CL below it (Sec. 2.6)."""
+    g = _small_sphere(8, 30.0)
+    for eps_h, ek in ((2.1025, 120.0), (4.0, 200.0)):
+        o = run.solve_point(*g, 2.4, [I.drude(2.4)], eps_h, (22.0, 0.0), ekin_keV=ek, want_img=True)
+        tot2 = losses.p_cl_tot(o["P_EELS"], o["P_ext"], o["P_sca_img"])
+        assert tot2 == pytest.approx(o["P_EELS"] - o["P_abs"], rel=1e-9, abs=1e-12 * abs(o["P_EELS"]))
+        if o["point"].beta_h.real < 1:
+            assert losses.p_cl_tot(o["P_EELS"], o["P_ext"], o["P_CL"]) == pytest.approx(o["P_CL"], rel=1e-10)
