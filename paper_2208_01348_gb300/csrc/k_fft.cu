@@ -229,6 +229,80 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass(LatticeDev L, MatvecArgs<
     fft_lines_io<true, true, NL>(Y, X, 1, es, L.px, tw, ldX, st);
 }
 
+// The x pass for Mx = 64 = 8 x 8 with the stage descriptors known at compile
+// time: the same shared-memory Stockham stages and D-hat product as k_xpass,
+// but every index division, mask and loop bound folds to constants.
+constexpr FftStage kX64S0{8, 1, 0, 8, 3, 8};   // radix 8 on length-1 sub-transforms
+constexpr FftStage kX64S1{8, 8, 3, 8, 3, 1};   // radix 8 on length-8 sub-transforms
+
+template <typename Rl, int W>
+__global__ void __launch_bounds__(FFT_THREADS) k_xpass64(LatticeDev L, MatvecArgs<Rl> a) {
+    using C = cx<Rl>;
+    constexpr int MX = 64;
+    const int s = blockIdx.z;
+    if (a.active && !a.active[s]) return;
+    const int ky = blockIdx.y, kz0 = blockIdx.x * W;
+    const int Mz = L.Mz, Nx = L.Nx;
+    constexpr int NL = 3 * W;
+    constexpr int es = NL + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* tw = reinterpret_cast<C*>(smem_raw);
+    C* A = tw + MX;
+    C* B = A + MX * es;
+    const C* twg = tw_of<Rl>(L, 0);
+    if (threadIdx.x < MX) tw[threadIdx.x] = twg[threadIdx.x];
+    __syncthreads();
+    const size_t plane = (size_t)Nx * Mz;
+    C* U0 = a.U + ((size_t)s * 3 * L.My + ky) * plane;
+    const size_t cstride = (size_t)L.My * plane;
+    const C zero = mk<C>(0.0, 0.0);
+    auto ld = [&](int l, int ix) -> C {
+        const int c = l / W, kz = kz0 + l % W;
+        return (ix < Nx && kz < Mz) ? U0[c * cstride + (size_t)ix * Mz + kz] : zero;
+    };
+    auto inA = [&](int l, int i) -> C { return A[i * es + l]; };
+    auto inB = [&](int l, int i) -> C { return B[i * es + l]; };
+    auto outA = [&](int l, int i, C v) { A[i * es + l] = v; };
+    auto outB = [&](int l, int i, C v) { B[i * es + l] = v; };
+    // forward x transforms of the 3W lines: U -> A -> B
+    fft_stage_f<8, false, true, NL>(kX64S0, tw, ld, outA);
+    __syncthreads();
+    fft_stage_f<8, false, true, NL>(kX64S1, tw, inA, outB);
+    __syncthreads();
+    // D-hat product, in place in B
+    const int hy = L.My / 2, hz = Mz / 2;
+    const int kyr = ky <= hy ? ky : L.My - ky;
+    const Rl sy = ky <= hy ? (Rl)1 : (Rl)-1;
+    const size_t cs = (size_t)L.Hy * L.Hx * L.Hz;
+    const C* Ds = a.Dr + (size_t)a.sys_slot[s] * 6 * cs + (size_t)kyr * L.Hx * L.Hz;
+#pragma unroll 2
+    for (int t = threadIdx.x; t < W * MX; t += FFT_THREADS) {
+        const int w = t % W, kx = t / W, kz = kz0 + w;
+        if (kz >= Mz) continue;
+        const int kxr = kx <= MX / 2 ? kx : MX - kx;
+        const int kzr = kz <= hz ? kz : Mz - kz;
+        const Rl sx = kx <= MX / 2 ? (Rl)1 : (Rl)-1;
+        const Rl sz = kz <= hz ? (Rl)1 : (Rl)-1;
+        const C* d = Ds + (size_t)kxr * L.Hz + kzr;
+        const C dxx = d[0], dxy = (sx * sy) * d[cs], dxz = (sx * sz) * d[2 * cs];
+        const C dyy = d[3 * cs], dyz = (sy * sz) * d[4 * cs], dzz = d[5 * cs];
+        C* e = B + kx * es + w;
+        const C Xv = e[0], Yv = e[W], Zv = e[2 * W];
+        e[0] = dxx * Xv + dxy * Yv + dxz * Zv;
+        e[W] = dxy * Xv + dyy * Yv + dyz * Zv;
+        e[2 * W] = dxz * Xv + dyz * Yv + dzz * Zv;
+    }
+    __syncthreads();
+    // inverse x transforms: B -> A -> U (first Nx outputs)
+    auto st = [&](int l, int ix, C v) {
+        const int c = l / W, kz = kz0 + l % W;
+        if (ix < Nx && kz < Mz) U0[c * cstride + (size_t)ix * Mz + kz] = v;
+    };
+    fft_stage_f<8, true, true, NL>(kX64S0, tw, inB, outA);
+    __syncthreads();
+    fft_stage_f<8, true, true, NL>(kX64S1, tw, inA, st);
+}
+
 // ---------------------------------------------------------------------------
 // D-hat build: G~'(R) on the padded lattice, R in units of d, for n_slot
 // wavenumbers kappa = k d.  Layout G[slot][comp][y][x][z].
@@ -683,7 +757,9 @@ template <typename Rl, int W>
 static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
     dim3 grid((L.Mz + W - 1) / W, L.My, a.S);
     count_launch();
-    k_xpass<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
+    const bool x64 = L.Mx == 64 && L.px.nst == 2 && L.px.st[0].R == 8;   // the 8 x 8 plan
+    if (x64) k_xpass64<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
+    else k_xpass<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
 }
 
 template <typename Rl, int CW> static size_t smem_slab(const LatticeDev& L) {
@@ -770,6 +846,7 @@ template <typename Rl, int W> static void prepare_w() {
     allow_smem(k_zfwd<Rl, W>);
     allow_smem(k_zinv<Rl, W>);
     allow_smem(k_xpass<Rl, W>);
+    allow_smem(k_xpass64<Rl, W>);
     allow_smem(k_axis<Rl, W, false, 1>);
     allow_smem(k_axis<Rl, W, true, 1>);
     allow_smem(k_axis<Rl, W, false, 2>);
