@@ -299,6 +299,15 @@ int eels_cl_total(int n, const double* p_eels, const double* p_ext, const double
  * host, Sec. 2.5): EELS_E_INVALID_ARG otherwise. */
 int eels_frank_tamm(double ekin_keV, eels_c128 eps_h, double* dp_dz);
 
+/* Extrapolation of one result to zero dipole size (Sec. 3.2): values[i]
+ * computed with dipole size d[i] (n >= 3 points, any length unit, d > 0)
+ * are fitted with a0 + a1 d + a2 d^2 by least squares with weights d^-6
+ * (errors taken to grow as d^3).  *value0 = a0; *ci95 = twice the standard
+ * error of a0 (residual-scaled covariance; 0 when n == 3), the nominal 95 %
+ * interval.  Host arrays.  EELS_E_INVALID_ARG for n < 3, d <= 0 or a
+ * singular fit. */
+int eels_extrapolate(int n, const double* d, const double* values, double* value0, double* ci95);
+
 /* The far-field direction grid the CL reduction uses (icosphere with
  * n_dir = 10*4^L+2 vertices): dirs [n_dir][3] unit vectors, weights
  * [n_dir] (sum 4 pi).  Host outputs. */

@@ -1193,6 +1193,45 @@ int eels_frank_tamm(double ekin_keV, eels_c128 eps_h, double* dp_dz) {
     return EELS_OK;
 }
 
+int eels_extrapolate(int n, const double* d, const double* values, double* value0, double* ci95) {
+    if (n < 3 || !d || !values || !value0 || !ci95) return EELS_E_INVALID_ARG;
+    // weighted least squares for v(d) = a0 + a1 d + a2 d^2, weights d^-6
+    // (errors growing as d^3); 3x3 normal matrix inverted by cofactors
+    double m[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, r[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        if (!(d[i] > 0)) return EELS_E_INVALID_ARG;
+        const double wi = 1.0 / std::pow(d[i], 6), b[3] = {1.0, d[i], d[i] * d[i]};
+        for (int p = 0; p < 3; ++p) {
+            r[p] += wi * b[p] * values[i];
+            for (int q = 0; q < 3; ++q) m[p][q] += wi * b[p] * b[q];
+        }
+    }
+    double inv[3][3];
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            const int p1 = (q + 1) % 3, p2 = (q + 2) % 3, q1 = (p + 1) % 3, q2 = (p + 2) % 3;
+            inv[p][q] = m[p1][q1] * m[p2][q2] - m[p1][q2] * m[p2][q1];   // cofactor of m[q][p]
+        }
+    const double det = m[0][0] * inv[0][0] + m[0][1] * inv[1][0] + m[0][2] * inv[2][0];
+    if (!(std::fabs(det) > 0)) return EELS_E_INVALID_ARG;
+    double a[3];
+    for (int p = 0; p < 3; ++p) {
+        for (int q = 0; q < 3; ++q) inv[p][q] /= det;
+    }
+    for (int p = 0; p < 3; ++p) a[p] = inv[p][0] * r[0] + inv[p][1] * r[1] + inv[p][2] * r[2];
+    *value0 = a[0];
+    *ci95 = 0.0;
+    if (n > 3) {
+        double chi2 = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const double e = values[i] - (a[0] + a[1] * d[i] + a[2] * d[i] * d[i]);
+            chi2 += e * e / std::pow(d[i], 6);
+        }
+        *ci95 = 2.0 * std::sqrt(chi2 / (n - 3) * inv[0][0]);
+    }
+    return EELS_OK;
+}
+
 int eels_directions(int n_dir, double* dirs, double* weights) {
     std::vector<double> d, w;
     if (!dirs || !weights || !icosphere(n_dir, d, w)) return EELS_E_INVALID_ARG;

@@ -99,6 +99,7 @@ _sig = {
     "eels_kernel_launches": (C.c_longlong, []),
     "eels_cl_total": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
     "eels_frank_tamm": (C.c_int, [C.c_double, eels_c128, _dp]),
+    "eels_extrapolate": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
     "eels_server_submit": (C.c_int, [_P, C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp,
@@ -352,6 +353,15 @@ def eels_frank_tamm(ekin_keV: float, eps_h: complex) -> float:
     r = C.c_double()
     _check(_lib.eels_frank_tamm(float(ekin_keV), eels_c128(complex(eps_h).real, complex(eps_h).imag), C.byref(r)))
     return r.value
+
+
+def eels_extrapolate(d, values):
+    """(value at d = 0, 95 % half-width) from results at dipole sizes d (Sec. 3.2)."""
+    dd_ = np.ascontiguousarray(d, dtype=np.float64)
+    vv = np.ascontiguousarray(values, dtype=np.float64)
+    v0, ci = C.c_double(), C.c_double()
+    _check(_lib.eels_extrapolate(len(dd_), _dptr(dd_), _dptr(vv), C.byref(v0), C.byref(ci)))
+    return v0.value, ci.value
 
 
 def eels_kernel_launches() -> int:

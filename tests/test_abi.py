@@ -101,3 +101,20 @@ def test_host_utilities_eq29_eq41_match_oracle():
     rng = np.random.default_rng(3)
     a, b, c = rng.random((3, 7, 2))
     assert np.allclose(dd.eels_cl_total(a, b, c), losses.p_cl_tot(a, b, c), rtol=0, atol=1e-15)
+
+
+def test_extrapolation_utility_matches_oracle():
+    """eels_extrapolate (Sec. 3.2) against the oracle on exact and noisy data."""
+    import numpy as np
+    from oracle.extrapolate import extrapolate_to_zero
+    from paper_2208_01348_gb300 import eelsdda as dd
+    d = 30.0 / np.array([128, 108, 91, 76, 64, 54, 45, 38, 32])
+    rng = np.random.default_rng(9)
+    for noise in (0.0, 1e-4, 1e-2):
+        y = 1.7 + 0.4 * d - 0.05 * d * d + noise * d ** 3 * rng.standard_normal(len(d))
+        v, ci = dd.eels_extrapolate(d, y)
+        rv, rci = extrapolate_to_zero(d, y)
+        assert v == pytest.approx(rv, rel=1e-12)
+        assert ci == pytest.approx(rci, rel=1e-7, abs=1e-9)   # noiseless: both are rounding-level
+    with pytest.raises(dd.EelsError):
+        dd.eels_extrapolate([1.0, 2.0], [1.0, 2.0])

@@ -399,3 +399,24 @@ def test_cl_total_forms_of_eq41_agree():
         assert tot2 == pytest.approx(o["P_EELS"] - o["P_abs"], rel=1e-9, abs=1e-12 * abs(o["P_EELS"]))
         if o["point"].beta_h.real < 1:
             assert losses.p_cl_tot(o["P_EELS"], o["P_ext"], o["P_CL"]) == pytest.approx(o["P_CL"], rel=1e-10)
+
+
+def test_extrapolation_to_zero_dipole_size_sec32():
+    """Sec. 3.2 extrapolation: exact for data that are a quadratic in d; value
+    and interval equal to an independent weighted polynomial fit (numpy's
+    polyfit with 1/sigma = d^-3 and its residual-scaled covariance); the
+    interval shrinks with the noise."""
+    from oracle.extrapolate import extrapolate_to_zero
+    nx = np.array([128, 108, 91, 76, 64, 54, 45, 38, 32])       # the paper's discretisations
+    d = 30.0 / nx
+    y = 2.5 - 0.3 * d + 0.07 * d * d
+    v, ci = extrapolate_to_zero(d, y)
+    assert v == pytest.approx(2.5, rel=1e-12) and ci < 1e-10
+    rng = np.random.default_rng(4)
+    noisy = y + 1e-3 * d ** 3 * rng.standard_normal(len(d))
+    v, ci = extrapolate_to_zero(d, noisy)
+    coef, cov = np.polyfit(d, noisy, 2, w=d ** -3.0, cov=True)
+    assert v == pytest.approx(coef[2], rel=1e-10)
+    assert ci == pytest.approx(2.0 * np.sqrt(cov[2, 2]), rel=1e-8)
+    v2, ci2 = extrapolate_to_zero(d, y + 1e-5 * d ** 3 * rng.standard_normal(len(d)))
+    assert ci2 < ci and abs(v2 - 2.5) < abs(v - 2.5) + 1e-9
