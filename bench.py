@@ -49,7 +49,7 @@ CPU_SAMPLE = {"spectrum": (100, 0), "small": (0, 0), "cherenkov": (50, 0), "rod"
 # measured on the kernels whose sources hash to TRAFFIC_SRC_HASH; reported as
 # null when the kernel sources differ from the measured ones.
 TRAFFIC_BYTES_PER_SYSTEM = 13_807_344       # profiles/fft_matvec_sphere32_64systems.md
-TRAFFIC_SRC_HASH = "64f79ff8c6b06b41"
+TRAFFIC_SRC_HASH = "8bb2c3504e21ef27"
 
 
 def kernel_src_hash() -> str:
