@@ -641,17 +641,19 @@ int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::v
 // QMR can stall or break down on a residual whose unconjugated square r^T r
 // is small, where BiCGStab, with its conjugated inner product, does not.
 // Systems still above eps_it finish with FP64 inner solves (BiCGStab after
-// FP32 rounds, for the same reason).  Lattices whose padded FFT grid has
-// fewer than 20,000 points go straight to FP64 inner solves with the chosen
-// solver: their matvec is bound by launch latency, so an FP64 iteration
-// costs about what an FP32 one does, and FP32 would only cost iterations
-// (measured on the serving stream's small rods and spheres: 2-7x faster).  EELS_FP64: FP64 inner solves with the chosen solver.
+// FP32 rounds, for the same reason).  Lattices whose padded FFT grid has at
+// most 65,536 points (40^3) go straight to FP64 inner solves with the chosen
+// solver: their matvec is bound by launch latency, so an FP64 iteration costs
+// little more than an FP32 one, while restarted FP32 rounds need up to 3x
+// the iterations on hard systems (measured on the serving stream: its rods
+// and spheres up to 40^3 solve 2-7x faster in FP64, one 36^3 request 2x
+// slower).  EELS_FP64: FP64 inner solves with the chosen solver.
 void refine_batch(eels_ctx* c, int S, const eels_opts* o, bool fp64, std::vector<int>& iters, std::vector<int>& refin,
                   std::vector<double>& resid) {
     cudaStream_t st = c->stream;
     int left = 1;
     const size_t m_pad = (size_t)c->L.Mx * c->L.My * c->L.Mz;
-    const bool fp32_rounds = !fp64 && m_pad >= (size_t)20000;
+    const bool fp32_rounds = !fp64 && m_pad > (size_t)65536;
     eels_opts ob = *o;
     ob.solver = EELS_BICGSTAB;
     if (fp32_rounds) {
