@@ -280,3 +280,26 @@ def test_async_solve_matches_blocking_solve(dd, ctx):
     for a, b in ((res.p_eels, ref.p_eels), (res.p_cl, ref.p_cl), (res.p_ext, ref.p_ext), (res.p, ref.p)):
         assert np.array_equal(a, b)
 
+
+
+def test_mixed_fp32_rounds_match_oracle_above_fp64_threshold(dd, ctx):
+    """A lattice whose padded grid (32 x 32 x 72) is above the size where the
+    mixed path switches to FP64 inner solves, so FP32 QMR rounds with FP64
+    refinement run; the oracle solves the same points with its own FFT
+    operator and GMRES."""
+    nx, ny, nz, d_nm = 16, 16, 36, 1.5
+    occ = I.box_occupancy(nx, ny, nz)
+    dd.eels_set_grid(ctx, occ, d_nm)
+    assert np.prod(dd.eels_padded_dims(ctx)) > 65536
+    e = np.array([2.6, 3.2])          # where the oracle's GMRES is quick
+    eps_p = I.drude(e)[:, None]
+    eps_h = np.full(2, 2.1025 + 0j)
+    beam = np.array([[nx * d_nm / 2 + 6.0, 0.0]])
+    o = dd.eels_default_opts(ekin_keV=100.0, precision=dd.EELS_MIXED, eps_it=1e-8)
+    res = dd.eels_solve(ctx, o, e, eps_p, eps_h, beam)
+    assert res.converged.all()
+    for ie in range(2):
+        ref = run.solve_point(nx, ny, nz, d_nm, occ, e[ie], eps_p[ie], eps_h[ie], beam[0], ekin_keV=100.0,
+                              method="fft", rtol=1e-11)
+        for key, got in (("P_EELS", res.p_eels), ("P_CL", res.p_cl), ("P_ext", res.p_ext), ("P_abs", res.p_abs)):
+            assert abs(got[ie, 0] - ref[key]) <= 1e-4 * abs(ref[key]), (key, got[ie, 0], ref[key])
