@@ -124,6 +124,13 @@ int eels_num_dipoles(const eels_ctx* ctx);
 /* Padded FFT extents chosen for the current grid. */
 int eels_padded_dims(const eels_ctx* ctx, int* mx, int* my, int* mz);
 
+/* Tile widths (z-adjacent lines per block, 8, 16 or 32) of the FFT x pass
+ * in FP32 and FP64 that the library picked for the current grid by timing
+ * each width on the first eels_solve after eels_set_grid (no counterpart in
+ * the paper: a tuning step of this implementation).  0 until that solve has
+ * run (a size heuristic is used meanwhile). */
+int eels_tile_widths(const eels_ctx* ctx, int* xw32, int* xw64);
+
 /*
  * Solve every (energy, beam) point and reduce the losses.  Host buffers.
  *   energy_eV [n_energy]; eps_p [n_energy][n_mat] (relative permittivity of

@@ -238,6 +238,7 @@ struct eels_ctx {
     int* pinned = nullptr;
     // cached inner-loop graph
     cudaGraphExec_t graph = nullptr;
+    bool tuned = false;            // x-pass tile widths timed for the current lattice
     std::vector<const void*> graph_key;
     long long graph_kernels = 0;
     // operator prepared by eels_prepare_operator
@@ -353,6 +354,8 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     if (matvec_smem_bytes(L, true) == 0) throw Fail{EELS_E_UNSUPPORTED, "grid: FFT tiles do not fit shared memory"};
     CK(cudaStreamSynchronize(c->stream));
     c->has_grid = true;
+    c->tuned = false;
+    c->L.xw32 = c->L.xw64 = 0;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
 }
 
@@ -786,6 +789,17 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         CK(cudaGetLastError());
         std::vector<int> it_b(S, 0), rf_b(S, 0);
         std::vector<double> rs_b(S, 0.0);
+        if (!c->tuned) {
+            // first solve on this lattice: time the x-pass tile widths on this
+            // batch (the x pass only scrambles the FFT scratch), before any
+            // inner-loop graph is captured; FP64 on a few systems only
+            c->L.xw32 = autotune_xpass<float>(L, mv_args<float>(c, S, c->u32.as<float2>(), c->kv[5].as<float2>(),
+                                                                 c->Dr32.as<float2>(), nullptr, true), st);
+            c->L.xw64 = autotune_xpass<double>(L, mv_args<double>(c, std::min(S, 8), c->x64.as<double2>(),
+                                                                   c->y64.as<double2>(), c->Dr64.as<double2>(),
+                                                                   nullptr, true), st);
+            c->tuned = true;
+        }
         refine_batch(c, S, o, fp64, it_b, rf_b, rs_b);
         // losses
         const int lblk = std::max(1, std::min(64, (c->N + 2047) / 2048));
@@ -944,6 +958,14 @@ int eels_set_grid(eels_ctx* c, const eels_grid* g) {
 }
 
 int eels_num_dipoles(const eels_ctx* c) { return (c && c->has_grid) ? c->N : 0; }
+
+int eels_tile_widths(const eels_ctx* c, int* xw32, int* xw64) {
+    if (!c || !xw32 || !xw64) return EELS_E_INVALID_ARG;
+    if (!c->has_grid) return EELS_E_NO_GRID;
+    *xw32 = c->L.xw32;
+    *xw64 = c->L.xw64;
+    return EELS_OK;
+}
 
 int eels_padded_dims(const eels_ctx* c, int* mx, int* my, int* mz) {
     if (!c || !c->has_grid) return EELS_E_NO_GRID;

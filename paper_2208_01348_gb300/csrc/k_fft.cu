@@ -813,8 +813,41 @@ template <typename Rl> static int pick_xpass_w(const LatticeDev& L) {
     return pick_w([&](int w) { return smem_xpass<Rl>(L, w); });
 }
 
+template <typename Rl> static int tuned_w(const LatticeDev& L) { return sizeof(Rl) == 4 ? L.xw32 : L.xw64; }
+
+template <typename Rl> static void xpass_w(const LatticeDev& L, const MatvecArgs<Rl>& a, int wx, cudaStream_t st) {
+    if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
+    else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
+    else xpass_launch<Rl, 8>(L, a, st);
+}
+
+template <typename Rl>
+int autotune_xpass(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+    int best = pick_xpass_w<Rl>(L);
+    float best_ms = 0.f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return best;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return best; }
+    bool first = true;
+    for (int w : {8, 16, 32}) {
+        if (smem_xpass<Rl>(L, w) > kSmemCap) continue;
+        xpass_w<Rl>(L, a, w, st);                   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) xpass_w<Rl>(L, a, w, st);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) break;
+        if (first || ms < best_ms) { best = w; best_ms = ms; first = false; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+template int autotune_xpass<float>(const LatticeDev&, const MatvecArgs<float>&, cudaStream_t);
+template int autotune_xpass<double>(const LatticeDev&, const MatvecArgs<double>&, cudaStream_t);
+
 template <typename Rl> static void xpass_any(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
-    const int wx = pick_xpass_w<Rl>(L);
+    const int wx = tuned_w<Rl>(L) ? tuned_w<Rl>(L) : pick_xpass_w<Rl>(L);
     if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
     else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
     else xpass_launch<Rl, 8>(L, a, st);

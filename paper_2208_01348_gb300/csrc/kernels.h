@@ -29,6 +29,7 @@ struct LatticeDev {
     const int* dip_cell;          // [N] internal dipole -> cell index ix + Nx (iy + Ny iz)
     const int2* col_range;        // [Ny][Nx] occupied iz range [first, last+1) (first = last = 0 if empty)
     FftPlan px, py, pz;
+    int xw32, xw64;               // x-pass tile width chosen by the autotuner (0: size heuristic)
     const double2* tw64x; const double2* tw64y; const double2* tw64z;   // exp(-2 pi i t / M)
     const float2* tw32x; const float2* tw32y; const float2* tw32z;
 };
@@ -61,6 +62,12 @@ void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, do
                        double2* Dr64, float2* Dr32, cudaStream_t st);
 
 size_t matvec_smem_bytes(const LatticeDev& L, bool fp64);
+// Times the x pass with every tile width whose shared memory fits, on the
+// systems of a (CUDA events on st; not during a stream capture), and returns
+// the fastest width.  The x pass transforms a.U in place: its contents are
+// lost.
+template <typename Rl>
+int autotune_xpass(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st);
 int matvec_passes(const LatticeDev& L, bool fp64);   // 3 (fused slabs) or 5
 
 // Raise the dynamic shared-memory limit of every kernel instance (call once

@@ -100,6 +100,7 @@ _sig = {
     "eels_cl_total": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
     "eels_frank_tamm": (C.c_int, [C.c_double, eels_c128, _dp]),
     "eels_extrapolate": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
+    "eels_tile_widths": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
     "eels_server_submit": (C.c_int, [_P, C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp,
@@ -362,6 +363,13 @@ def eels_extrapolate(d, values):
     v0, ci = C.c_double(), C.c_double()
     _check(_lib.eels_extrapolate(len(dd_), _dptr(dd_), _dptr(vv), C.byref(v0), C.byref(ci)))
     return v0.value, ci.value
+
+
+def eels_tile_widths(ctx):
+    """(FP32, FP64) x-pass tile widths timed on the first solve of the grid (0: not yet)."""
+    a, b = C.c_int(), C.c_int()
+    _check(_lib.eels_tile_widths(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
 
 
 def eels_kernel_launches() -> int:
