@@ -394,6 +394,7 @@ def main():
 
     # roofline of the FFT matvec (the dominant kernel set) on this workload's systems
     S = len(w.energies_eV)
+    tiles = dd.eels_tile_widths(ctx)
     dd.eels_prepare_operator(ctx, w.energies_eV, w.eps_p, w.eps_h)
     n = dd.eels_num_dipoles(ctx)
     mx, my, mz = dd.eels_padded_dims(ctx)
@@ -447,12 +448,12 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64" if prec == dd.EELS_MIXED else "f64",
         "data": "synthetic (Drude permittivities stand in for tabulated optical data)",
         "config": {"workload": w.name, "points_per_gpu": w.n_points, "dipoles": n, "fft": [mx, my, mz],
-                   "precision": args.precision, "solver": args.solver, "eps_it": 1e-8, "eps_inner": 1e-5, "n_dir": w.n_dir,
+                   "precision": args.precision, "solver": args.solver, "x_tile": list(tiles), "eps_it": 1e-8, "eps_inner": 1e-5, "n_dir": w.n_dir,
                    "l2": "working set of a step > L2 (several GB of per-system vectors)",
                    "iters_mean": float(np.mean(res.iters)), "residual_max": float(np.max(res.residual))},
         "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-        "roofline": {"bound": "hbm", "kernel": "fft_matvec (3 launches: k_slab_fwd, k_xpass, k_slab_inv)",
+        "roofline": {"bound": "hbm", "kernel": "fft_matvec (3 launches: k_slab_fwd64, k_xpass64, k_slab_inv64 on a 64^3 grid)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic, "ms_per_matvec": mv_ms, "systems": S,
                      "alg_bytes": alg_bytes},
