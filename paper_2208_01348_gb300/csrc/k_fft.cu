@@ -229,16 +229,29 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass(LatticeDev L, MatvecArgs<
     fft_lines_io<true, true, NL>(Y, X, 1, es, L.px, tw, ldX, st);
 }
 
-// The x pass for Mx = 64 = 8 x 8 with the stage descriptors known at compile
-// time: the same shared-memory Stockham stages and D-hat product as k_xpass,
-// but every index division, mask and loop bound folds to constants.
-constexpr FftStage kX64S0{8, 1, 0, 8, 3, 8};   // radix 8 on length-1 sub-transforms
-constexpr FftStage kX64S1{8, 8, 3, 8, 3, 1};   // radix 8 on length-8 sub-transforms
+// The x pass for the common lengths Mx = 64 (8 x 8) and Mx = 128 (8 x 8 x 2)
+// with the stage descriptors known at compile time: the same shared-memory
+// Stockham stages and D-hat product as k_xpass, but every index division,
+// mask and loop bound folds to constants, and the block has one thread per
+// radix-8 butterfly of a stage (3W lines x MX/8).
+__host__ __device__ constexpr int cilog2(int v) { return (v > 0 && (v & (v - 1)) == 0) ? (v == 1 ? 0 : 1 + cilog2(v / 2)) : -1; }
+__host__ __device__ constexpr FftStage cstage(int len, int r, int ns) {
+    return FftStage{r, ns, cilog2(ns), len / r, cilog2(len / r), len / (ns * r)};
+}
 
-template <typename Rl, int W>
-__global__ void __launch_bounds__(FFT_THREADS) k_xpass64(LatticeDev L, MatvecArgs<Rl> a) {
+template <int MX> struct XPlan;
+template <> struct XPlan<64> { static constexpr int n = 2, r[3] = {8, 8, 1}; };
+template <> struct XPlan<128> { static constexpr int n = 3, r[3] = {8, 8, 2}; };
+
+template <typename Rl, int W, int MX>
+__global__ void __launch_bounds__(3 * W * (MX / 8), (W == 16 && MX == 64 && sizeof(Rl) == 4) ? 4 : 1)
+k_xpassc(LatticeDev L, MatvecArgs<Rl> a) {
     using C = cx<Rl>;
-    constexpr int MX = 64;
+    using P = XPlan<MX>;
+    constexpr int NT = 3 * W * (MX / 8);
+    constexpr FftStage S0 = cstage(MX, P::r[0], 1);
+    constexpr FftStage S1 = cstage(MX, P::r[1], P::r[0]);
+    constexpr FftStage S2 = cstage(MX, P::n == 3 ? P::r[2] : 2, P::r[0] * P::r[1]);
     const int s = blockIdx.z;
     if (a.active && !a.active[s]) return;
     const int ky = blockIdx.y, kz0 = blockIdx.x * W;
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass64(LatticeDev L, MatvecArg
     C* A = tw + MX;
     C* B = A + MX * es;
     const C* twg = tw_of<Rl>(L, 0);
-    if (threadIdx.x < MX) tw[threadIdx.x] = twg[threadIdx.x];
+    for (int t = threadIdx.x; t < MX; t += NT) tw[t] = twg[t];
     __syncthreads();
     const size_t plane = (size_t)Nx * Mz;
     C* U0 = a.U + ((size_t)s * 3 * L.My + ky) * plane;
@@ -260,23 +273,32 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass64(LatticeDev L, MatvecArg
         const int c = l / W, kz = kz0 + l % W;
         return (ix < Nx && kz < Mz) ? U0[c * cstride + (size_t)ix * Mz + kz] : zero;
     };
+    auto st = [&](int l, int ix, C v) {
+        const int c = l / W, kz = kz0 + l % W;
+        if (ix < Nx && kz < Mz) U0[c * cstride + (size_t)ix * Mz + kz] = v;
+    };
     auto inA = [&](int l, int i) -> C { return A[i * es + l]; };
     auto inB = [&](int l, int i) -> C { return B[i * es + l]; };
     auto outA = [&](int l, int i, C v) { A[i * es + l] = v; };
     auto outB = [&](int l, int i, C v) { B[i * es + l] = v; };
-    // forward x transforms of the 3W lines: U -> A -> B
-    fft_stage_f<8, false, true, NL>(kX64S0, tw, ld, outA);
+    // forward x transforms of the 3W lines: U -> A -> B (-> A)
+    fft_stage_f<P::r[0], false, true, NL>(S0, tw, ld, outA);
     __syncthreads();
-    fft_stage_f<8, false, true, NL>(kX64S1, tw, inA, outB);
+    fft_stage_f<P::r[1], false, true, NL>(S1, tw, inA, outB);
     __syncthreads();
-    // D-hat product, in place in B
+    if (P::n == 3) {
+        fft_stage_f<(P::n == 3 ? P::r[2] : 2), false, true, NL>(S2, tw, inB, outA);
+        __syncthreads();
+    }
+    C* X = P::n == 3 ? A : B;         // holds the spectrum
+    // D-hat product, in place
     const int hy = L.My / 2, hz = Mz / 2;
     const int kyr = ky <= hy ? ky : L.My - ky;
     const Rl sy = ky <= hy ? (Rl)1 : (Rl)-1;
     const size_t cs = (size_t)L.Hy * L.Hx * L.Hz;
     const C* Ds = a.Dr + (size_t)a.sys_slot[s] * 6 * cs + (size_t)kyr * L.Hx * L.Hz;
 #pragma unroll 2
-    for (int t = threadIdx.x; t < W * MX; t += FFT_THREADS) {
+    for (int t = threadIdx.x; t < W * MX; t += NT) {
         const int w = t % W, kx = t / W, kz = kz0 + w;
         if (kz >= Mz) continue;
         const int kxr = kx <= MX / 2 ? kx : MX - kx;
@@ -286,21 +308,25 @@ __global__ void __launch_bounds__(FFT_THREADS) k_xpass64(LatticeDev L, MatvecArg
         const C* d = Ds + (size_t)kxr * L.Hz + kzr;
         const C dxx = d[0], dxy = (sx * sy) * d[cs], dxz = (sx * sz) * d[2 * cs];
         const C dyy = d[3 * cs], dyz = (sy * sz) * d[4 * cs], dzz = d[5 * cs];
-        C* e = B + kx * es + w;
+        C* e = X + kx * es + w;
         const C Xv = e[0], Yv = e[W], Zv = e[2 * W];
         e[0] = dxx * Xv + dxy * Yv + dxz * Zv;
         e[W] = dxy * Xv + dyy * Yv + dyz * Zv;
         e[2 * W] = dxz * Xv + dyz * Yv + dzz * Zv;
     }
     __syncthreads();
-    // inverse x transforms: B -> A -> U (first Nx outputs)
-    auto st = [&](int l, int ix, C v) {
-        const int c = l / W, kz = kz0 + l % W;
-        if (ix < Nx && kz < Mz) U0[c * cstride + (size_t)ix * Mz + kz] = v;
-    };
-    fft_stage_f<8, true, true, NL>(kX64S0, tw, inB, outA);
-    __syncthreads();
-    fft_stage_f<8, true, true, NL>(kX64S1, tw, inA, st);
+    // inverse x transforms back to U (first Nx outputs)
+    if (P::n == 3) {
+        fft_stage_f<P::r[0], true, true, NL>(S0, tw, inA, outB);
+        __syncthreads();
+        fft_stage_f<P::r[1], true, true, NL>(S1, tw, inB, outA);
+        __syncthreads();
+        fft_stage_f<(P::n == 3 ? P::r[2] : 2), true, true, NL>(S2, tw, inA, st);
+    } else {
+        fft_stage_f<P::r[0], true, true, NL>(S0, tw, inB, outA);
+        __syncthreads();
+        fft_stage_f<P::r[1], true, true, NL>(S1, tw, inA, st);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -757,9 +783,20 @@ template <typename Rl, int W>
 static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
     dim3 grid((L.Mz + W - 1) / W, L.My, a.S);
     count_launch();
-    const bool x64 = L.Mx == 64 && L.px.nst == 2 && L.px.st[0].R == 8;   // the 8 x 8 plan
-    if (x64) k_xpass64<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
-    else k_xpass<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
+    const auto& px = L.px;
+    const bool x64 = L.Mx == 64 && px.nst == 2 && px.st[0].R == 8 && px.st[1].R == 8;
+    const bool x128 = L.Mx == 128 && px.nst == 3 && px.st[0].R == 8 && px.st[1].R == 8 && px.st[2].R == 2;
+    if (x64) {
+        k_xpassc<Rl, W, 64><<<grid, 3 * W * 8, smem_xpass<Rl>(L, W), st>>>(L, a);
+        return;
+    }
+    if constexpr (W <= 16) {                         // 3W x 16 threads per block
+        if (x128) {
+            k_xpassc<Rl, W, 128><<<grid, 3 * W * 16, smem_xpass<Rl>(L, W), st>>>(L, a);
+            return;
+        }
+    }
+    k_xpass<Rl, W><<<grid, FFT_THREADS, smem_xpass<Rl>(L, W), st>>>(L, a);
 }
 
 template <typename Rl, int CW> static size_t smem_slab(const LatticeDev& L) {
@@ -879,7 +916,8 @@ template <typename Rl, int W> static void prepare_w() {
     allow_smem(k_zfwd<Rl, W>);
     allow_smem(k_zinv<Rl, W>);
     allow_smem(k_xpass<Rl, W>);
-    allow_smem(k_xpass64<Rl, W>);
+    allow_smem(k_xpassc<Rl, W, 64>);
+    if constexpr (W <= 16) allow_smem(k_xpassc<Rl, W, 128>);
     allow_smem(k_axis<Rl, W, false, 1>);
     allow_smem(k_axis<Rl, W, true, 1>);
     allow_smem(k_axis<Rl, W, false, 2>);

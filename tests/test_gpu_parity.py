@@ -82,7 +82,7 @@ def _random_grid(dims, seed, frac=0.7, nmat=1):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (3, 4, 5), (7, 3, 2), (5, 9, 6), (12, 12, 12), (13, 6, 17),
-                                  (32, 5, 3), (31, 4, 6)])
+                                  (32, 5, 3), (31, 4, 6), (64, 3, 2)])
 def test_matvec_equals_dense_oracle(dd, ctx, dims):
     nx, ny, nz = dims
     nmat = 2 if nx * ny * nz > 8 else 1
