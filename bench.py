@@ -454,7 +454,7 @@ def main():
         "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
         "roofline": {"bound": "hbm", "kernel": (f"fft_matvec (3 launches: slab forward, x pass, slab inverse; {mx}x{my}x{mz} FFT"
-                               + (", k_slab_fwd64 / k_xpass64 / k_slab_inv64)" if (mx, my, mz) == (64, 64, 64) else ")")),
+                               + (", k_slab_fwd64 / k_xpassc<float,16,64> / k_slab_inv64)" if (mx, my, mz) == (64, 64, 64) else ")")),
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic, "ms_per_matvec": mv_ms, "systems": S,
                      "alg_bytes": alg_bytes},

@@ -587,6 +587,7 @@ __device__ __forceinline__ void fft64_warp(float2 (&v)[8], float2* tile, int q, 
 
 struct Slab64Smem {
     float2 tw[64];
+    float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];   // this system's per-material coefficients
     float2 S[64 * R64_SLS];
     float2 tile[FFT_THREADS / 32][R64_TILE];
 };
@@ -601,10 +602,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
     const int nwarp = blockDim.x >> 5;
     const float2* twg = tw_of<float>(L, 1);          // My = Mz = 64: the y and z tables coincide
     if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
+    if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
     __syncthreads();
     float2* tile = sm.tile[warp];
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
-    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
     const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
     const C zero = make_float2(0.f, 0.f);
     // y transforms of the Nz columns, 4 per warp: gathered from x, into S
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
             v[r] = zero;
             if (y < Ny && iz < Nz) {
                 const int dip = cm[y * Nz + iz];
-                if (dip >= 0) v[r] = xs[dip] * to_f(cf[L.mat[dip]]);
+                if (dip >= 0) v[r] = xs[dip] * sm.cf[L.mat[dip]];
             }
         }
         fft64_warp<false>(v, tile, q, p, sm.tw);
@@ -655,6 +656,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
     const int nwarp = blockDim.x >> 5;
     const float2* twg = tw_of<float>(L, 2);
     if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
+    if (threadIdx.x < EELS_MAX_MAT) {
+        sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+        sm.dg[threadIdx.x] = to_f(a.diag[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+    }
     __syncthreads();
     float2* tile = sm.tile[warp];
     // inverse z transforms of the 64 rows of U, first Nz outputs into S
@@ -676,8 +681,6 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
     // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     C* ys = a.y + ((size_t)s * 3 + c) * L.N;
-    const double2* cf = a.coef + (size_t)s * EELS_MAX_MAT;
-    const double2* dg = a.diag + (size_t)s * EELS_MAX_MAT;
     const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
     float dot0 = 0.f, dot1 = 0.f;
     for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
@@ -695,7 +698,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
             if (dip < 0) continue;
             const int m = L.mat[dip];
             const C xv = xs[dip];
-            const C yv = to_f(dg[m]) * xv - to_f(cf[m]) * (invM * v[k]);
+            const C yv = sm.dg[m] * xv - sm.cf[m] * (invM * v[k]);
             ys[dip] = yv;
             dot0 += xv.x * yv.x - xv.y * yv.y;
             dot1 += xv.x * yv.y + xv.y * yv.x;
