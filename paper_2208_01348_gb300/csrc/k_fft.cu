@@ -239,11 +239,51 @@ __host__ __device__ constexpr FftStage cstage(int len, int r, int ns) {
     return FftStage{r, ns, cilog2(ns), len / r, cilog2(len / r), len / (ns * r)};
 }
 
+// First forward stage (sub-transform length 1, no twiddles) whose inputs
+// j + r L/R lie in the zero padding for r >= R/2 when HALF (the lattice fills
+// exactly the first half of the line): those inputs are compile-time zeros.
+template <int R, int NL, int LEN, bool HALF, typename C, class In, class Out>
+__device__ __forceinline__ void xstage_first(In in, Out out) {
+    constexpr int nb = LEN / R;
+    for (int t = threadIdx.x; t < NL * nb; t += blockDim.x) {
+        const int line = t % NL, j = t / NL;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = (!HALF || r < R / 2) ? in(line, j + r * nb) : mk<C>(0.0, 0.0);
+        Dft<R, false, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) out(line, j * R + r, v[r]);
+    }
+}
+
+// Last inverse stage (sub-transform length L/R, twiddle stride 1): with HALF
+// only the outputs j + r L/R with r < R/2 (the lattice half) are formed.
+template <int R, int NL, int LEN, bool HALF, typename C, class In, class Out>
+__device__ __forceinline__ void xstage_last_inv(const C* __restrict__ tw, In in, Out out) {
+    constexpr int nb = LEN / R;
+    for (int t = threadIdx.x; t < NL * nb; t += blockDim.x) {
+        const int line = t % NL, j = t / NL;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = in(line, j + r * nb);
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C w = tw[r * j];
+            w.y = -w.y;
+            v[r] = v[r] * w;
+        }
+        Dft<R, true, C>::run(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (!HALF || r < R / 2) out(line, j + r * nb, v[r]);
+    }
+}
+
 template <int MX> struct XPlan;
 template <> struct XPlan<64> { static constexpr int n = 2, r[3] = {8, 8, 1}; };
 template <> struct XPlan<128> { static constexpr int n = 3, r[3] = {8, 8, 2}; };
 
-template <typename Rl, int W, int MX>
+template <typename Rl, int W, int MX, bool HALF>
 __global__ void __launch_bounds__(3 * W * (MX / 8), (W == 16 && MX == 64 && sizeof(Rl) == 4) ? 4 : 1)
 k_xpassc(LatticeDev L, MatvecArgs<Rl> a) {
     using C = cx<Rl>;
@@ -282,7 +322,7 @@ k_xpassc(LatticeDev L, MatvecArgs<Rl> a) {
     auto outA = [&](int l, int i, C v) { A[i * es + l] = v; };
     auto outB = [&](int l, int i, C v) { B[i * es + l] = v; };
     // forward x transforms of the 3W lines: U -> A -> B (-> A)
-    fft_stage_f<P::r[0], false, true, NL>(S0, tw, ld, outA);
+    xstage_first<P::r[0], NL, MX, HALF, C>(ld, outA);
     __syncthreads();
     fft_stage_f<P::r[1], false, true, NL>(S1, tw, inA, outB);
     __syncthreads();
@@ -321,11 +361,11 @@ k_xpassc(LatticeDev L, MatvecArgs<Rl> a) {
         __syncthreads();
         fft_stage_f<P::r[1], true, true, NL>(S1, tw, inB, outA);
         __syncthreads();
-        fft_stage_f<(P::n == 3 ? P::r[2] : 2), true, true, NL>(S2, tw, inA, st);
+        xstage_last_inv<(P::n == 3 ? P::r[2] : 2), NL, MX, HALF, C>(tw, inA, st);
     } else {
         fft_stage_f<P::r[0], true, true, NL>(S0, tw, inB, outA);
         __syncthreads();
-        fft_stage_f<P::r[1], true, true, NL>(S1, tw, inA, st);
+        xstage_last_inv<P::r[1], NL, MX, HALF, C>(tw, inA, st);
     }
 }
 
@@ -789,13 +829,16 @@ static void xpass_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStrea
     const auto& px = L.px;
     const bool x64 = L.Mx == 64 && px.nst == 2 && px.st[0].R == 8 && px.st[1].R == 8;
     const bool x128 = L.Mx == 128 && px.nst == 3 && px.st[0].R == 8 && px.st[1].R == 8 && px.st[2].R == 2;
+    const bool half = 2 * L.Nx == L.Mx;             // the lattice fills exactly half of each line
     if (x64) {
-        k_xpassc<Rl, W, 64><<<grid, 3 * W * 8, smem_xpass<Rl>(L, W), st>>>(L, a);
+        if (half) k_xpassc<Rl, W, 64, true><<<grid, 3 * W * 8, smem_xpass<Rl>(L, W), st>>>(L, a);
+        else k_xpassc<Rl, W, 64, false><<<grid, 3 * W * 8, smem_xpass<Rl>(L, W), st>>>(L, a);
         return;
     }
     if constexpr (W <= 16) {                         // 3W x 16 threads per block
         if (x128) {
-            k_xpassc<Rl, W, 128><<<grid, 3 * W * 16, smem_xpass<Rl>(L, W), st>>>(L, a);
+            if (half) k_xpassc<Rl, W, 128, true><<<grid, 3 * W * 16, smem_xpass<Rl>(L, W), st>>>(L, a);
+            else k_xpassc<Rl, W, 128, false><<<grid, 3 * W * 16, smem_xpass<Rl>(L, W), st>>>(L, a);
             return;
         }
     }
@@ -919,8 +962,12 @@ template <typename Rl, int W> static void prepare_w() {
     allow_smem(k_zfwd<Rl, W>);
     allow_smem(k_zinv<Rl, W>);
     allow_smem(k_xpass<Rl, W>);
-    allow_smem(k_xpassc<Rl, W, 64>);
-    if constexpr (W <= 16) allow_smem(k_xpassc<Rl, W, 128>);
+    allow_smem(k_xpassc<Rl, W, 64, true>);
+    allow_smem(k_xpassc<Rl, W, 64, false>);
+    if constexpr (W <= 16) {
+        allow_smem(k_xpassc<Rl, W, 128, true>);
+        allow_smem(k_xpassc<Rl, W, 128, false>);
+    }
     allow_smem(k_axis<Rl, W, false, 1>);
     allow_smem(k_axis<Rl, W, true, 1>);
     allow_smem(k_axis<Rl, W, false, 2>);
