@@ -632,6 +632,10 @@ struct Slab64Smem {
     float2 tile[FFT_THREADS / 32][R64_TILE];
 };
 
+// HALF: Ny = Nz = 32, so the lattice fills exactly the first half of every
+// 64-point line: the zero padding and the discarded outputs are known at
+// compile time and their arithmetic drops out.
+template <bool HALF>
 __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, MatvecArgs<float> a) {
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -656,7 +660,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
         for (int r = 0; r < 8; ++r) {
             const int y = p + 8 * r;
             v[r] = zero;
-            if (y < Ny && iz < Nz) {
+            if ((HALF ? r < 4 : y < Ny) && iz < Nz) {
                 const int dip = cm[y * Nz + iz];
                 if (dip >= 0) v[r] = xs[dip] * sm.cf[L.mat[dip]];
             }
@@ -677,7 +681,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             const int z = p + 8 * r;
-            v[r] = z < Nz ? sm.S[ky * R64_SLS + z] : zero;
+            v[r] = (HALF ? r < 4 : z < Nz) ? sm.S[ky * R64_SLS + z] : zero;
         }
         fft64_warp<false>(v, tile, q, p, sm.tw);
 #pragma unroll
@@ -685,6 +689,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
     }
 }
 
+template <bool HALF>
 __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, MatvecArgs<float> a, float invM) {
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -714,7 +719,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int z = p + 8 * k;
-            if (z < Nz) sm.S[ky * R64_SLS + z] = v[k];
+            if (HALF ? k < 4 : z < Nz) sm.S[ky * R64_SLS + z] = v[k];
         }
     }
     __syncthreads();
@@ -733,7 +738,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int y = p + 8 * k;
-            if (y >= Ny) continue;
+            if (HALF ? k >= 4 : y >= Ny) continue;
             const int dip = cm[y * Nz + iz];
             if (dip < 0) continue;
             const int m = L.mat[dip];
@@ -875,8 +880,14 @@ template <> bool slab64_launch<float>(const LatticeDev& L, const MatvecArgs<floa
     if (L.My != 64 || L.Mz != 64) return false;
     dim3 grid(L.Nx, a.S * 3);
     count_launch();
-    if (!inv) k_slab_fwd64<<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a);
-    else k_slab_inv64<<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a, (float)(1.0 / ((double)L.Mx * L.My * L.Mz)));
+    const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
+    if (L.Ny == 32 && L.Nz == 32) {
+        if (!inv) k_slab_fwd64<true><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a);
+        else k_slab_inv64<true><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a, invM);
+    } else {
+        if (!inv) k_slab_fwd64<false><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a);
+        else k_slab_inv64<false><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a, invM);
+    }
     return true;
 }
 
@@ -981,8 +992,10 @@ void prepare_far_kernels();
 void prepare_kernels() {
     prepare_w<float, 8>(); prepare_w<float, 16>(); prepare_w<float, 32>();
     prepare_w<double, 8>(); prepare_w<double, 16>(); prepare_w<double, 32>();
-    allow_smem(k_slab_fwd64);
-    allow_smem(k_slab_inv64);
+    allow_smem(k_slab_fwd64<true>);
+    allow_smem(k_slab_fwd64<false>);
+    allow_smem(k_slab_inv64<true>);
+    allow_smem(k_slab_inv64<false>);
     prepare_far_kernels();
 }
 
