@@ -63,3 +63,36 @@ def line_integral_I1(r, omega, v, gamma_h, x0, y0, z0=0.0, q=Q_ELECTRON, conjuga
     dx, dy, b = _transverse(r, x0, y0)
     sgn = -1.0 if conjugate else 1.0
     return q / (2.0 * np.pi) * np.exp(sgn * 1j * omega * (r[:, 2] - z0) / v) * kv(0, omega * b / (gamma_h * v))
+
+
+def beam_frame(direction):
+    """Orthonormal frame (e1, e2, n) of an electron moving along `direction`:
+    the rotation that takes z to n by the smallest angle (about the axis
+    z x n; a half turn about x when n = -z) applied to (x, y, z).  For n = z
+    it is the lattice frame, so (x0, y0) keep their meaning."""
+    n = np.asarray(direction, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    z = np.array([0.0, 0.0, 1.0])
+    axis = np.cross(z, n)
+    s = np.linalg.norm(axis)
+    c = float(n[2])
+    if s < 1e-15:
+        Rm = np.eye(3) if c > 0 else np.diag([1.0, -1.0, -1.0])
+    else:
+        k = axis / s
+        K = np.array([[0, -k[2], k[1]], [k[2], 0, -k[0]], [-k[1], k[0], 0]])
+        Rm = np.eye(3) + s * K + (1 - c) * (K @ K)      # Rodrigues' rotation formula
+    return Rm[:, 0], Rm[:, 1], Rm[:, 2]
+
+
+def fields_along(r, omega, v, m_h, gamma_h, x0, y0, direction, q=Q_ELECTRON):
+    """E_inc and E_a for an electron moving along `direction` through the
+    point x0 e1 + y0 e2 of its frame (beam_frame), phase reference there:
+    Eq. 25 and the first line of Eq. 34 evaluated in the frame (e1, e2, n)
+    and rotated back to the lattice frame.  Returns two complex [N,3]."""
+    e1, e2, n = beam_frame(direction)
+    Rm = np.stack([e1, e2, n], axis=1)            # columns: frame axes in lattice coordinates
+    rp = (r - (x0 * e1 + y0 * e2)) @ Rm           # coordinates in the beam frame
+    E = incident_field(rp, omega, v, m_h, gamma_h, 0.0, 0.0, q=q) @ Rm.T
+    Ea = auxiliary_field(rp, omega, v, m_h, gamma_h, 0.0, 0.0, q=q) @ Rm.T
+    return E, Ea

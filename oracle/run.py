@@ -49,7 +49,7 @@ class Point:
     d: float
 
 
-def setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None, v=None):
+def setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None, v=None, direction=None):
     if v is None:
         v = physics.electron_speed(ekin_keV)
     omega = float(physics.omega_of(energy_eV))
@@ -62,8 +62,11 @@ def setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None
     a_cm = physics.polarizability_cm(m2, d)
     a = physics.polarizability_rr(a_cm, k)
     x0, y0 = beam_nm[0] * NM, beam_nm[1] * NM
-    E = field.incident_field(r, omega, v, m_h, gamma, x0, y0)
-    Ea = field.auxiliary_field(r, omega, v, m_h, gamma, x0, y0)
+    if direction is None:
+        E = field.incident_field(r, omega, v, m_h, gamma, x0, y0)
+        Ea = field.auxiliary_field(r, omega, v, m_h, gamma, x0, y0)
+    else:
+        E, Ea = field.fields_along(r, omega, v, m_h, gamma, x0, y0, direction)
     return Point(omega, k, m_h, beta, gamma, v, idx, r, a, a_cm, E, Ea, complex(eps_h), (nx, ny, nz), d)
 
 
@@ -129,8 +132,8 @@ def p_si(pt: Point, p_t):
 
 
 def solve_point(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None, v=None,
-                method="lu", want_cl=True, want_img=False, rtol=1e-12):
-    pt = setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=ekin_keV, v=v)
+                method="lu", want_cl=True, want_img=False, rtol=1e-12, direction=None):
+    pt = setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=ekin_keV, v=v, direction=direction)
     if method == "lu":
         p_t = solve_lu(pt)
     else:

@@ -420,3 +420,24 @@ def test_extrapolation_to_zero_dipole_size_sec32():
     assert ci == pytest.approx(2.0 * np.sqrt(cov[2, 2]), rel=1e-8)
     v2, ci2 = extrapolate_to_zero(d, y + 1e-5 * d ** 3 * rng.standard_normal(len(d)))
     assert ci2 < ci and abs(v2 - 2.5) < abs(v - 2.5) + 1e-9
+
+
+def test_electron_direction_rotation_invariance():
+    """An electron along x or y past a lattice sphere (symmetric under the
+    quarter turns that take z to x or y) gives the probabilities of the
+    electron along z with the same (x0, y0) in its frame; the frame of z is
+    the lattice frame; an oblique direction changes the result."""
+    g = _small_sphere(8, 16.0)
+    base = run.solve_point(*g, 2.4, [I.drude(2.4)], 2.1025, (12.0, 3.0), ekin_keV=100.0)
+    same_z = run.solve_point(*g, 2.4, [I.drude(2.4)], 2.1025, (12.0, 3.0), ekin_keV=100.0, direction=(0, 0, 1))
+    for key in ("P_EELS", "P_CL", "P_ext", "P_abs"):
+        assert same_z[key] == pytest.approx(base[key], rel=1e-13), key
+    for n in ((1, 0, 0), (0, 1, 0), (0, 0, -1)):
+        o = run.solve_point(*g, 2.4, [I.drude(2.4)], 2.1025, (12.0, 3.0), ekin_keV=100.0, direction=n)
+        for key in ("P_EELS", "P_CL", "P_ext", "P_abs"):
+            assert o[key] == pytest.approx(base[key], rel=1e-10), (n, key)
+    e1, e2, nn = field.beam_frame((1.0, 2.0, 2.0))
+    assert np.allclose(np.stack([e1, e2, nn]) @ np.stack([e1, e2, nn]).T, np.eye(3), atol=1e-14)
+    assert np.allclose(np.cross(e1, e2), nn, atol=1e-14) and np.allclose(nn, np.array([1, 2, 2]) / 3.0)
+    obl = run.solve_point(*g, 2.4, [I.drude(2.4)], 2.1025, (12.0, 3.0), ekin_keV=100.0, direction=(1, 1, 1))
+    assert abs(obl["P_EELS"] - base["P_EELS"]) > 1e-6 * abs(base["P_EELS"])
