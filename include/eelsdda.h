@@ -86,6 +86,12 @@ typedef struct {
     int max_batch;           /* (energy, beam) systems solved together; 0 = choose from free memory */
     int inner_max_iter;      /* EELS_MIXED: FP32 iterations per inner solve before the FP64 residual is
                                 recomputed and the inner solve restarts (0 = max_iter) */
+    double beam_dir[3];      /* direction of the electron (any non-zero length; default 0, 0, 1).  A
+                                beam (x0, y0) is the trajectory through x0 e1 + y0 e2 along n, where
+                                (e1, e2, n) is the lattice frame turned by the smallest rotation that
+                                takes z to n (a half turn about x for n = -z); the phase of Eq. 25 is
+                                referred to that point.  The paper's electron moves along z (Sec. 2.2;
+                                the direction option of its solver, Sec. S5) */
 } eels_opts;
 
 typedef struct {
@@ -185,6 +191,11 @@ int eels_bessel_k01_dev(const eels_c128* z, eels_c128* k0, eels_c128* k1, int n,
  * NULL).  eps_h relative permittivity; beam at (x0, y0). */
 int eels_incident_field(eels_ctx* ctx, double ekin_keV, double energy_eV, eels_c128 eps_h,
                         eels_beam beam, eels_c128* e_inc, eels_c128* e_aux);
+
+/* eels_incident_field for an electron along beam_dir (see eels_opts.beam_dir;
+ * NULL means +z): Eq. 25 and Eq. 34 written in the electron's frame. */
+int eels_incident_field_dir(eels_ctx* ctx, double ekin_keV, double energy_eV, eels_c128 eps_h,
+                            eels_beam beam, const double* beam_dir, eels_c128* e_inc, eels_c128* e_aux);
 
 /* y = A x for the dipole matrix of the current grid, A = diag(alpha~^-1) - G~
  * in SI (m^-3), x and y host [n_vec][N][3].  precision selects the FP64 or the

@@ -396,6 +396,97 @@ EnergyPar energy_params(double ekin, double e_eV, cd eps_h, int n_mat, const eel
     return p;
 }
 
+// Frame (e1, e2, n) of an electron moving along dir: the smallest rotation
+// taking z to n applied to (x, y, z) (Rodrigues' formula about z x n; a half
+// turn about x when n = -z).  The trajectory passes through x0 e1 + y0 e2.
+struct BeamFrame {
+    double e1[3], e2[3], n[3];
+    bool along_z;
+};
+
+BeamFrame beam_frame(const double* dir) {
+    BeamFrame f{};
+    const double len = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(len > 0) || !std::isfinite(len)) throw Fail{EELS_E_INVALID_ARG, "beam_dir must be a finite non-zero vector"};
+    const double n[3] = {dir[0] / len, dir[1] / len, dir[2] / len};
+    double R[3][3];
+    const double kx = -n[1], ky = n[0];                 // z x n
+    const double sn = std::sqrt(kx * kx + ky * ky), cs = n[2];
+    if (sn < 1e-15) {
+        const double sg = cs > 0 ? 1.0 : -1.0;
+        const double Rm[3][3] = {{1, 0, 0}, {0, sg, 0}, {0, 0, sg}};
+        std::memcpy(R, Rm, sizeof(R));
+    } else {
+        const double ux = kx / sn, uy = ky / sn;      // unit axis (ux, uy, 0)
+        const double K[3][3] = {{0, 0, uy}, {0, 0, -ux}, {-uy, ux, 0}};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double kk = 0;
+                for (int m = 0; m < 3; ++m) kk += K[i][m] * K[m][j];
+                R[i][j] = (i == j ? 1.0 : 0.0) + sn * K[i][j] + (1.0 - cs) * kk;
+            }
+    }
+    for (int i = 0; i < 3; ++i) {
+        f.e1[i] = R[i][0];
+        f.e2[i] = R[i][1];
+        f.n[i] = R[i][2];
+    }
+    f.along_z = dir[0] == 0.0 && dir[1] == 0.0 && dir[2] > 0.0;
+    if (f.along_z) {
+        const double e1[3] = {1, 0, 0}, e2[3] = {0, 1, 0}, ez[3] = {0, 0, 1};
+        std::memcpy(f.e1, e1, sizeof(e1));
+        std::memcpy(f.e2, e2, sizeof(e2));
+        std::memcpy(f.n, ez, sizeof(ez));
+    }
+    return f;
+}
+
+// Fills the electron fields of a SysField for beam b (lattice units).
+void set_beam(SysField& sf, const BeamFrame& f, const eels_beam& beam, double d_nm) {
+    const double x0 = beam.x0_nm / d_nm, y0 = beam.y0_nm / d_nm;
+    sf.x0 = x0;
+    sf.y0 = y0;
+    sf.px = x0 * f.e1[0] + y0 * f.e2[0];
+    sf.py = x0 * f.e1[1] + y0 * f.e2[1];
+    sf.pz = x0 * f.e1[2] + y0 * f.e2[2];
+    sf.nx = f.n[0];
+    sf.ny = f.n[1];
+    sf.nz = f.n[2];
+    sf.along_z = f.along_z ? 1 : 0;
+}
+
+// An oblique electron must not cross an occupied cell: slab test of the line
+// p + t n against every occupied unit cube (lattice units).
+void check_beams_dir(eels_ctx* c, int n_beam, const eels_beam* beams, const BeamFrame& f) {
+    for (int b = 0; b < n_beam; ++b) {
+        SysField sf{};
+        set_beam(sf, f, beams[b], c->d_nm);
+        const double p[3] = {sf.px, sf.py, sf.pz}, n[3] = {f.n[0], f.n[1], f.n[2]};
+        if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2]))
+            throw Fail{EELS_E_INVALID_ARG, "beam position not finite"};
+        for (int iz = 0; iz < c->nz; ++iz)
+            for (int iy = 0; iy < c->ny; ++iy)
+                for (int ix = 0; ix < c->nx; ++ix) {
+                    if (c->cellmap_h[((size_t)iz * c->ny + iy) * c->nx + ix] < 0) continue;
+                    const double lo[3] = {ix - 0.5 * c->nx, iy - 0.5 * c->ny, iz - 0.5 * c->nz};
+                    double t0 = -1e300, t1 = 1e300;
+                    bool hit = true;
+                    for (int a = 0; a < 3 && hit; ++a) {
+                        if (std::fabs(n[a]) < 1e-300) {
+                            hit = p[a] >= lo[a] && p[a] <= lo[a] + 1.0;
+                        } else {
+                            double ta = (lo[a] - p[a]) / n[a], tb = (lo[a] + 1.0 - p[a]) / n[a];
+                            if (ta > tb) std::swap(ta, tb);
+                            t0 = std::max(t0, ta);
+                            t1 = std::min(t1, tb);
+                            hit = t0 <= t1;
+                        }
+                    }
+                    if (hit) throw Fail{EELS_E_BEAM_INSIDE, "beam " + std::to_string(b) + " crosses an occupied cell"};
+                }
+    }
+}
+
 void check_beams(eels_ctx* c, int n_beam, const eels_beam* beams) {
     for (int b = 0; b < n_beam; ++b) {
         const double x = beams[b].x0_nm / c->d_nm + 0.5 * c->nx, y = beams[b].y0_nm / c->d_nm + 0.5 * c->ny;
@@ -685,7 +776,9 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
     if (o->solver != EELS_QMR && o->solver != EELS_BICGSTAB) throw Fail{EELS_E_INVALID_ARG, "unknown solver"};
     if (!(o->eps_it > 0) || o->max_iter <= 0) throw Fail{EELS_E_INVALID_ARG, "eps_it and max_iter must be positive"};
     if (p_cl && o->n_dir <= 0) throw Fail{EELS_E_INVALID_ARG, "p_cl requested with n_dir = 0"};
-    check_beams(c, n_beam, beams);
+    const BeamFrame frame = beam_frame(o->beam_dir);
+    if (frame.along_z) check_beams(c, n_beam, beams);
+    else check_beams_dir(c, n_beam, beams, frame);
     CK(cudaSetDevice(c->device));
     cudaStream_t st = c->stream;
     const LatticeDev& L = c->L;
@@ -771,8 +864,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
             sf[s].inv_gamma = d2(1.0 / p.gamma);
             sf[s].pref_unit = d2(p.pref_unit);
             sf[s].wdv = p.wdv;
-            sf[s].x0 = beams[b].x0_nm / c->d_nm;
-            sf[s].y0 = beams[b].y0_nm / c->d_nm;
+            set_beam(sf[s], frame, beams[b], c->d_nm);
             for (int m = 0; m < EELS_MAX_MAT; ++m) {
                 coef[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? d2(p.sa[m]) : make_double2(0, 0);
                 wabs[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? p.wabs[m] : 0.0;
@@ -783,7 +875,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         }
         h2d(c->sysf, sf, st); h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->wabs, wabs, st);
         h2d(c->wdv, wdv, st); h2d(c->slot, slot, st); h2d(c->kappa_sys, kap, st);
-        launch_incident_field(L, S, c->sysf.as<SysField>(), c->e64.as<double2>(), st);
+        launch_incident_field(L, S, c->sysf.as<SysField>(), frame.along_z, c->e64.as<double2>(), st);
         launch_rhs_init(L, S, c->e64.as<double2>(), c->coef.as<double2>(), c->b64.as<double2>(), c->x64.as<double2>(),
                         c->r64.as<double2>(), st);
         // y = A x for x = 0: refinement rounds recompute y only for the systems they update
@@ -808,7 +900,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         c->lpart.ensure((size_t)S * lblk * 8 * sizeof(double));
         c->lsums.ensure((size_t)S * 5 * sizeof(double));
         launch_losses(L, S, c->e64.as<double2>(), c->x64.as<double2>(), c->coef.as<double2>(), c->wabs.as<double>(),
-                      c->wdv.as<double>(), c->lpart.as<double>(), lblk, c->lsums.as<double>(), st);
+                      c->wdv.as<double>(), c->sysf.as<SysField>(), c->lpart.as<double>(), lblk, c->lsums.as<double>(), st);
         std::vector<double> ls((size_t)S * 5), fs(S, 0.0);
         CK(cudaMemcpyAsync(ls.data(), c->lsums.p, ls.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         if (p_cl || p_out)
@@ -900,6 +992,9 @@ void eels_default_opts(eels_opts* o) {
     o->n_dir = 2562;
     o->max_batch = 0;
     o->inner_max_iter = 1000;
+    o->beam_dir[0] = 0.0;
+    o->beam_dir[1] = 0.0;
+    o->beam_dir[2] = 1.0;
 }
 
 int eels_create(eels_ctx** out, int device, void* cuda_stream) {
@@ -1009,26 +1104,30 @@ int eels_bessel_k01_dev(const eels_c128* z, eels_c128* k0, eels_c128* k1, int n,
     return cudaGetLastError() == cudaSuccess ? EELS_OK : EELS_E_CUDA;
 }
 
-int eels_incident_field(eels_ctx* c, double ekin_keV, double energy_eV, eels_c128 eps_h, eels_beam beam,
-                        eels_c128* e_inc, eels_c128* e_aux) {
+int eels_incident_field_dir(eels_ctx* c, double ekin_keV, double energy_eV, eels_c128 eps_h, eels_beam beam,
+                            const double* beam_dir, eels_c128* e_inc, eels_c128* e_aux) {
     if (!c) return EELS_E_INVALID_ARG;
     return guarded(c, [&] {
         if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
-        check_beams(c, 1, &beam);
+        const double zdir[3] = {0.0, 0.0, 1.0};
+        const BeamFrame frame = beam_frame(beam_dir ? beam_dir : zdir);
+        if (frame.along_z) check_beams(c, 1, &beam);
+        else check_beams_dir(c, 1, &beam, frame);
         CK(cudaSetDevice(c->device));
         const double d_m = c->d_nm * 1e-9;
         eels_c128 one{1.0, 0.0};
         EnergyPar p = energy_params(ekin_keV, energy_eV, cz(eps_h), 1, &one, d_m);
         SysField sf;
         sf.kt = d2(p.wdv / p.gamma); sf.inv_gamma = d2(1.0 / p.gamma); sf.pref_unit = d2(p.pref_unit);
-        sf.wdv = p.wdv; sf.x0 = beam.x0_nm / c->d_nm; sf.y0 = beam.y0_nm / c->d_nm;
+        sf.wdv = p.wdv;
+        set_beam(sf, frame, beam, c->d_nm);
         std::vector<SysField> sv(1, sf);
         cudaStream_t st = c->stream;
         h2d(c->sysf, sv, st);
         const size_t n3 = (size_t)3 * c->N;
         c->e64.ensure(n3 * sizeof(double2));
         c->y64.ensure(n3 * sizeof(double2));
-        launch_incident_field(c->L, 1, c->sysf.as<SysField>(), c->e64.as<double2>(), st);
+        launch_incident_field(c->L, 1, c->sysf.as<SysField>(), frame.along_z, c->e64.as<double2>(), st);
         launch_aux_field(c->L, 1, c->sysf.as<SysField>(), c->e64.as<double2>(), c->y64.as<double2>(), st);
         std::vector<double2> h(n3), ha(n3);
         CK(cudaMemcpyAsync(h.data(), c->e64.p, n3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -1043,6 +1142,11 @@ int eels_incident_field(eels_ctx* c, double ekin_keV, double energy_eV, eels_c12
             }
         return EELS_OK;
     });
+}
+
+int eels_incident_field(eels_ctx* c, double ekin_keV, double energy_eV, eels_c128 eps_h, eels_beam beam,
+                        eels_c128* e_inc, eels_c128* e_aux) {
+    return eels_incident_field_dir(c, ekin_keV, energy_eV, eps_h, beam, nullptr, e_inc, e_aux);
 }
 
 int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, const eels_c128* eps_p, eels_c128 eps_h,

@@ -643,7 +643,7 @@ void launch_to_f32(size_t n, const double2* a, float2* b, cudaStream_t st) {
 // Per block partial sums over dipoles: sum E_a.u (3 comps), sum conj(E).u, sum |u|^2 w.
 // E_a = (-E_x, -E_y, E_z) exp(-2 i w (z - z0)/v)   (Eq. 34, second form)
 __global__ void k_losses(LatticeDev L, const double2* e, const double2* x, const double2* coef, const double* wabs,
-                         const double* wdv, double* part, int nblk) {
+                         const double* wdv, const SysField* sys, double* part, int nblk) {
     const int s = blockIdx.y, blk = blockIdx.x;
     const size_t N = (size_t)L.N, off = (size_t)s * 3 * N;
     const int chunk = (L.N + nblk - 1) / nblk;
@@ -655,12 +655,26 @@ __global__ void k_losses(LatticeDev L, const double2* e, const double2* x, const
         const double2 cf = coef[(size_t)s * EELS_MAX_MAT + m];
         const double2 ux = cf * x[off + i], uy = cf * x[off + N + i], uz = cf * x[off + 2 * N + i];
         const double2 ex = e[off + i], ey = e[off + N + i], ez = e[off + 2 * N + i];
-        const int iz = L.dip_cell[i] / (L.Nx * L.Ny);
-        const double zr = (iz + 0.5) - 0.5 * L.Nz;
-        double sn, cs;
-        sincos(-2.0 * w * zr, &sn, &cs);
-        const double2 ph = make_double2(cs, sn);
-        const double2 ea = ph * (ez * uz - ex * ux - ey * uy);
+        const int cell = L.dip_cell[i];
+        const int iz = cell / (L.Nx * L.Ny);
+        double2 ea;
+        if (sys[s].along_z) {
+            const double zr = (iz + 0.5) - 0.5 * L.Nz;
+            double sn, cs;
+            sincos(-2.0 * w * zr, &sn, &cs);
+            const double2 ph = make_double2(cs, sn);
+            ea = ph * (ez * uz - ex * ux - ey * uy);
+        } else {   // E_a . u = exp(-2 i w z'/v) (2 (E.n)(n.u) - E.u)
+            const SysField& p = sys[s];
+            const int ix = cell % L.Nx, iy = (cell / L.Nx) % L.Ny;
+            const double zp = ((ix + 0.5) - 0.5 * L.Nx - p.px) * p.nx + ((iy + 0.5) - 0.5 * L.Ny - p.py) * p.ny +
+                              ((iz + 0.5) - 0.5 * L.Nz - p.pz) * p.nz;
+            double sn, cs;
+            sincos(-2.0 * w * zp, &sn, &cs);
+            const double2 ph = make_double2(cs, sn);
+            const double2 en = p.nx * ex + p.ny * ey + p.nz * ez, un = p.nx * ux + p.ny * uy + p.nz * uz;
+            ea = ph * (2.0 * (en * un) - (ex * ux + ey * uy + ez * uz));
+        }
         const double2 ec = conj_(ex) * ux + conj_(ey) * uy + conj_(ez) * uz;
         v[0] += ea.x; v[1] += ea.y; v[2] += ec.x; v[3] += ec.y;
         v[4] += (abs2_(ux) + abs2_(uy) + abs2_(uz)) * wabs[(size_t)s * EELS_MAX_MAT + m];
@@ -683,9 +697,10 @@ __global__ void k_sum_parts(int S, int nblk, int stride, int nval, const double*
 }
 
 void launch_losses(const LatticeDev& L, int S, const double2* e, const double2* x, const double2* coef,
-                   const double* wabs, const double* wdv, double* part, int nblk, double* sums, cudaStream_t st) {
+                   const double* wabs, const double* wdv, const SysField* sys, double* part, int nblk, double* sums,
+                   cudaStream_t st) {
     count_launch();
-    k_losses<<<dim3(nblk, S), 256, 0, st>>>(L, e, x, coef, wabs, wdv, part, nblk);
+    k_losses<<<dim3(nblk, S), 256, 0, st>>>(L, e, x, coef, wabs, wdv, sys, part, nblk);
     count_launch();
     k_sum_parts<<<(S + 127) / 128, 128, 0, st>>>(S, nblk, 8, 5, part, sums);
 }

@@ -80,9 +80,16 @@ struct SysField {
     double2 inv_gamma;  // 1 / gamma_h
     double2 pref_unit;  // phase of the Eq. 25 prefactor
     double wdv;         // omega d / v
-    double x0, y0;      // beam, lattice units relative to the lattice centre
+    double x0, y0;      // beam, lattice units relative to the lattice centre (electron along +z)
+    // electron along an arbitrary direction n: the trajectory passes through p
+    // (lattice units relative to the lattice centre); along_z selects the +z
+    // kernels, for which p = (x0, y0, 0) and n = z
+    double px, py, pz, nx, ny, nz;
+    int along_z;
 };
-void launch_incident_field(const LatticeDev& L, int S, const SysField* sys, double2* e, cudaStream_t st);
+// along_z: every system's electron moves along +z (the per-column kernel)
+void launch_incident_field(const LatticeDev& L, int S, const SysField* sys, bool along_z, double2* e,
+                           cudaStream_t st);
 void launch_aux_field(const LatticeDev& L, int S, const SysField* sys, const double2* e, double2* ea, cudaStream_t st);
 void launch_bessel(const double2* z, double2* k0, double2* k1, int n, cudaStream_t st);
 

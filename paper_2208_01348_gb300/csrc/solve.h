@@ -90,7 +90,8 @@ void launch_to_f32(size_t n, const double2* a, float2* b, cudaStream_t st);
 // ---- Loss reductions (Eq. 32, 17, 18) on u = coef * x (scaled dipoles) ----
 // per system sums: [0..1] sum E_a . u, [2..3] sum conj(E_inc) . u, [4] sum |u|^2 w_abs[mat]
 void launch_losses(const LatticeDev& L, int S, const double2* e, const double2* x, const double2* coef,
-                   const double* wabs, const double* wdv, double* part, int nblk, double* sums, cudaStream_t st);
+                   const double* wabs, const double* wdv, const SysField* sys, double* part, int nblk, double* sums,
+                   cudaStream_t st);
 // u = coef * x in FP32 and FP64
 void launch_scaled_dipoles(const LatticeDev& L, int S, const double2* x, const double2* coef, double2* u64, float2* u32,
                            cudaStream_t st);

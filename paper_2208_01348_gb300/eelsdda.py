@@ -52,7 +52,8 @@ class eels_beam(C.Structure):
 class eels_opts(C.Structure):
     _fields_ = [("ekin_keV", C.c_double), ("precision", C.c_int), ("solver", C.c_int),
                 ("eps_it", C.c_double), ("eps_inner", C.c_double), ("max_iter", C.c_int),
-                ("n_dir", C.c_int), ("max_batch", C.c_int), ("inner_max_iter", C.c_int)]
+                ("n_dir", C.c_int), ("max_batch", C.c_int), ("inner_max_iter", C.c_int),
+                ("beam_dir", C.c_double * 3)]
 
 
 class eels_point_stats(C.Structure):
@@ -92,6 +93,7 @@ _sig = {
     "eels_query_footprint": (C.c_int, [C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, C.POINTER(C.c_size_t)]),
     "eels_bessel_k01_dev": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "eels_incident_field": (C.c_int, [_P, C.c_double, C.c_double, eels_c128, eels_beam, _cp, _cp]),
+    "eels_incident_field_dir": (C.c_int, [_P, C.c_double, C.c_double, eels_c128, eels_beam, _dp, _cp, _cp]),
     "eels_apply_matrix": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _cp, eels_c128, C.c_int, _cp, _cp]),
     "eels_directions": (C.c_int, [C.c_int, _dp, _dp]),
     "eels_prepare_operator": (C.c_int, [_P, C.c_int, _dp, C.c_int, _cp, _cp]),
@@ -149,6 +151,8 @@ def eels_default_opts(**kw) -> eels_opts:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
+        if k == "beam_dir":
+            v = (C.c_double * 3)(*[float(c) for c in v])
         setattr(o, k, v)
     return o
 
@@ -294,13 +298,20 @@ def eels_bessel_k01_dev(z_ptr: int, k0_ptr: int, k1_ptr: int, n: int, stream: in
     _check(_lib.eels_bessel_k01_dev(_P(z_ptr), _P(k0_ptr), _P(k1_ptr), n, _P(stream) if stream else None))
 
 
-def eels_incident_field(ctx, ekin_keV: float, energy_eV: float, eps_h: complex, beam_nm):
+def eels_incident_field(ctx, ekin_keV: float, energy_eV: float, eps_h: complex, beam_nm, beam_dir=None):
+    """E_inc and E_a at the dipoles (SI); beam_dir None: electron along +z."""
     n = eels_num_dipoles(ctx)
     e = np.zeros((n, 3), dtype=np.complex128)
     ea = np.zeros((n, 3), dtype=np.complex128)
     eh = complex(eps_h)
-    _check(_lib.eels_incident_field(ctx, ekin_keV, energy_eV, eels_c128(eh.real, eh.imag),
-                                    eels_beam(float(beam_nm[0]), float(beam_nm[1])), _cptr(e), _cptr(ea)), ctx)
+    bm = eels_beam(float(beam_nm[0]), float(beam_nm[1]))
+    if beam_dir is None:
+        code = _lib.eels_incident_field(ctx, ekin_keV, energy_eV, eels_c128(eh.real, eh.imag), bm, _cptr(e), _cptr(ea))
+    else:
+        dv = np.ascontiguousarray(beam_dir, dtype=np.float64)
+        code = _lib.eels_incident_field_dir(ctx, ekin_keV, energy_eV, eels_c128(eh.real, eh.imag), bm, _dptr(dv),
+                                            _cptr(e), _cptr(ea))
+    _check(code, ctx)
     return e, ea
 
 

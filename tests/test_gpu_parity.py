@@ -321,3 +321,45 @@ def test_tile_autotuning_keeps_matvec_bits(dd, ctx):
     y_after = [dd.eels_apply_matrix(ctx, pr, 2.2, eps_p, eps_h, x) for pr in (dd.EELS_FP64, dd.EELS_MIXED)]
     for a, b in zip(y_before, y_after):
         assert np.array_equal(a, b)
+
+
+# ------------------------------------------------------------------ electron direction
+@pytest.mark.parametrize("direction,eps_h", [((1.0, 2.0, 2.0), 2.1025), ((0.0, 0.0, -1.0), 4.0 + 0.05j),
+                                             ((1.0, 0.0, 0.0), 1.0), ((0.3, -0.2, 0.9), 4.0)])
+def test_incident_field_along_a_direction(dd, ctx, direction, eps_h):
+    w = I.config_small_sphere()
+    g = w.grid
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    beam = (16.0, 3.0)
+    E, Ea = dd.eels_incident_field(ctx, 150.0, 2.6, eps_h, beam, beam_dir=direction)
+    pt = run.setup(g.nx, g.ny, g.nz, g.d_nm, g.occ, 2.6, [1.0], eps_h, beam, ekin_keV=150.0, direction=direction)
+    assert rel(E, pt.E_inc) < 1e-12
+    assert rel(Ea, pt.E_a) < 1e-12
+
+
+def test_oblique_electron_solves_match_lu_and_rotations_agree(dd, ctx):
+    """An electron along (1, 1, 1) against the oracle's LU solve (FP64 and
+    mixed), and electrons along x and z with the same (x0, y0) past the
+    lattice sphere give the same probabilities (a quarter turn maps one onto
+    the other); an oblique line through the particle is refused."""
+    w = I.config_small_sphere()
+    g = w.grid
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    beam = np.array([[15.0, 2.0]])
+    for prec, eps, tol in ((dd.EELS_FP64, 1e-12, 1e-10), (dd.EELS_MIXED, 1e-8, 1e-4)):
+        o = dd.eels_default_opts(ekin_keV=100.0, precision=prec, eps_it=eps, beam_dir=(1.0, 1.0, 1.0))
+        res = dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, beam, want_p=True)
+        ref = run.solve_point(g.nx, g.ny, g.nz, g.d_nm, g.occ, w.energies_eV[0], w.eps_p[0], w.eps_h[0], beam[0],
+                              ekin_keV=100.0, direction=(1.0, 1.0, 1.0))
+        _check_point(res, 0, 0, ref, tol, tol)
+    out = {}
+    for n in ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0)):
+        o = dd.eels_default_opts(ekin_keV=100.0, precision=dd.EELS_FP64, eps_it=1e-12, beam_dir=n)
+        out[n] = dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, beam)
+    for n in ((1.0, 0.0, 0.0), (0.0, 1.0, 0.0)):
+        for a, b in ((out[n].p_eels, out[(0.0, 0.0, 1.0)].p_eels), (out[n].p_cl, out[(0.0, 0.0, 1.0)].p_cl)):
+            assert np.allclose(a, b, rtol=1e-9, atol=0)
+    o = dd.eels_default_opts(ekin_keV=100.0, beam_dir=(1.0, 1.0, 0.0))
+    with pytest.raises(dd.EelsError) as e:
+        dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, [[0.0, 1.0]])
+    assert e.value.code == dd.EELS_E_BEAM_INSIDE
