@@ -767,6 +767,219 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
 }
 
 // ---------------------------------------------------------------------------
+// The same register-resident slab passes for My = Mz = 128: lane = q + 4p
+// holds the 16 elements p + 8r of its line.  A length-16 DFT over the
+// registers (4 x 4), the twiddles exp(-+2 pi i p k / 128), a transpose that
+// gives lane j the values of k = j and k = j + 8 from the 8 lanes of the line,
+// and two length-8 DFTs leave element j + 8m of the transform in register m
+// of lane j (m = 2 k2 + h for k = j + 8h + 16 k2): the same (lane, register)
+// <-> index map as the input.  Slab buffer rows of 68 (= 4 mod 16) values.
+// ---------------------------------------------------------------------------
+constexpr int R128_QS = 148;  // transpose tile strides (8-byte units): line -> 4, lane -> 1 (mod 16)
+constexpr int R128_PS = 17;
+constexpr int R128_TILE = 4 * R128_QS;
+constexpr int R128_SLS = 68;
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    // n = n1 + 4 n2, k = k1 + 4 k2: length-4 DFTs over n2, twiddles w16^(n1 k1), length-4 DFTs over n1
+    float2 a[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+        float2 t[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
+        Dft<4, INV, float2>::run(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) a[n1][k1] = t[k1];
+    }
+    // w16^(n1 k1) for n1 k1 in {1, 2, 3, 4, 6, 9}: cos/sin of multiples of pi/8
+    const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
+    const float sg = INV ? 1.f : -1.f;
+    auto rot = [&](float2 x, float c, float s) { return make_float2(x.x * c - x.y * s * sg, x.x * s * sg + x.y * c); };
+    a[1][1] = rot(a[1][1], c1, s1);        // w^1
+    a[1][2] = rot(a[1][2], h, h);          // w^2
+    a[1][3] = rot(a[1][3], s1, c1);        // w^3
+    a[2][1] = rot(a[2][1], h, h);          // w^2
+    a[2][2] = rot(a[2][2], 0.f, 1.f);      // w^4
+    a[2][3] = rot(a[2][3], -h, h);         // w^6
+    a[3][1] = rot(a[3][1], s1, c1);        // w^3
+    a[3][2] = rot(a[3][2], -h, h);         // w^6
+    a[3][3] = rot(a[3][3], -c1, -s1);      // w^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+        Dft<4, INV, float2>::run(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
+    }
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft128_warp(float2 (&v)[16], float2* tile, int q, int p, const float2* tw) {
+    dft16<INV>(v);
+#pragma unroll
+    for (int k = 1; k < 16; ++k) {
+        float2 w = tw[p * k];
+        if (INV) w.y = -w.y;
+        v[k] = v[k] * w;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) tile[q * R128_QS + p * R128_PS + k] = v[k];
+    __syncwarp();
+    float2 a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = tile[q * R128_QS + i * R128_PS + p];
+        b[i] = tile[q * R128_QS + i * R128_PS + p + 8];
+    }
+    __syncwarp();
+    Dft<8, INV, float2>::run(a);
+    Dft<8, INV, float2>::run(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+        v[2 * k2] = a[k2];
+        v[2 * k2 + 1] = b[k2];
+    }
+}
+
+struct Slab128Smem {
+    float2 tw[128];
+    float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];
+    float2 S[128 * R128_SLS];
+    float2 tile[FFT_THREADS / 32][R128_TILE];
+};
+
+// HALF: Ny = Nz = 64 (the lattice fills exactly half of every line).
+template <bool HALF>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_fwd128(LatticeDev L, MatvecArgs<float> a) {
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Slab128Smem& sm = *reinterpret_cast<Slab128Smem*>(smem_raw);
+    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
+    const int nwarp = blockDim.x >> 5;
+    const float2* twg = tw_of<float>(L, 1);          // My = Mz = 128: the y and z tables coincide
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) sm.tw[t] = twg[t];
+    if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+    __syncthreads();
+    float2* tile = sm.tile[warp];
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    const C zero = make_float2(0.f, 0.f);
+    // y transforms of the Nz columns, 4 per warp: gathered from x, into S
+    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
+        const int iz = iz0 + q;
+        C v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int y = p + 8 * r;
+            v[r] = zero;
+            if ((HALF ? r < 8 : y < Ny) && iz < Nz) {
+                const int dip = cm[y * Nz + iz];
+                if (dip >= 0) v[r] = xs[dip] * sm.cf[L.mat[dip]];
+            }
+        }
+        fft128_warp<false>(v, tile, q, p, sm.tw);
+        if (iz < Nz) {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) sm.S[(p + 8 * m) * R128_SLS + iz] = v[m];
+        }
+    }
+    __syncthreads();
+    // z transforms of the 128 rows, 4 per warp: from S, written to U
+    C* U = a.U + (((size_t)s * 3 + c) * 128 * L.Nx + ix) * 128;
+    const size_t row = (size_t)L.Nx * 128;
+    for (int ky0 = warp * 4; ky0 < 128; ky0 += nwarp * 4) {
+        const int ky = ky0 + q;
+        C v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int z = p + 8 * r;
+            v[r] = (HALF ? r < 8 : z < Nz) ? sm.S[ky * R128_SLS + z] : zero;
+        }
+        fft128_warp<false>(v, tile, q, p, sm.tw);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) U[(size_t)ky * row + p + 8 * m] = v[m];
+    }
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_inv128(LatticeDev L, MatvecArgs<float> a, float invM) {
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Slab128Smem& sm = *reinterpret_cast<Slab128Smem*>(smem_raw);
+    __shared__ float red[2 * FFT_THREADS / 32];
+    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
+    if (a.active && !a.active[s]) return;
+    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
+    const int nwarp = blockDim.x >> 5;
+    const float2* twg = tw_of<float>(L, 2);
+    for (int t = threadIdx.x; t < 128; t += blockDim.x) sm.tw[t] = twg[t];
+    if (threadIdx.x < EELS_MAX_MAT) {
+        sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+        sm.dg[threadIdx.x] = to_f(a.diag[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+    }
+    __syncthreads();
+    float2* tile = sm.tile[warp];
+    // inverse z transforms of the 128 rows of U, first Nz outputs into S
+    const C* U = a.U + (((size_t)s * 3 + c) * 128 * L.Nx + ix) * 128;
+    const size_t row = (size_t)L.Nx * 128;
+    for (int ky0 = warp * 4; ky0 < 128; ky0 += nwarp * 4) {
+        const int ky = ky0 + q;
+        C v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = U[(size_t)ky * row + p + 8 * r];
+        fft128_warp<true>(v, tile, q, p, sm.tw);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int z = p + 8 * m;
+            if (HALF ? m < 8 : z < Nz) sm.S[ky * R128_SLS + z] = v[m];
+        }
+    }
+    __syncthreads();
+    // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
+    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+    C* ys = a.y + ((size_t)s * 3 + c) * L.N;
+    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    float dot0 = 0.f, dot1 = 0.f;
+    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
+        const int iz = iz0 + q;
+        C v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = iz < Nz ? sm.S[(p + 8 * r) * R128_SLS + iz] : make_float2(0.f, 0.f);
+        fft128_warp<true>(v, tile, q, p, sm.tw);
+        if (iz >= Nz) continue;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int y = p + 8 * m;
+            if (HALF ? m >= 8 : y >= Ny) continue;
+            const int dip = cm[y * Nz + iz];
+            if (dip < 0) continue;
+            const int mt = L.mat[dip];
+            const C xv = xs[dip];
+            const C yv = sm.dg[mt] * xv - sm.cf[mt] * (invM * v[m]);
+            ys[dip] = yv;
+            dot0 += xv.x * yv.x - xv.y * yv.y;
+            dot1 += xv.x * yv.y + xv.y * yv.x;
+        }
+    }
+    if (a.dot_part) {
+        for (int o = 16; o > 0; o >>= 1) {
+            dot0 += __shfl_xor_sync(0xffffffffu, dot0, o);
+            dot1 += __shfl_xor_sync(0xffffffffu, dot1, o);
+        }
+        if (lane == 0) { red[2 * warp] = dot0; red[2 * warp + 1] = dot1; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s0 = 0, s1 = 0;
+            for (int i = 0; i < nwarp; ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
+            double* pp = a.dot_part + (((size_t)s * 3 + c) * L.Nx + ix) * 4;
+            pp[0] = s0; pp[1] = s1; pp[2] = 0.0; pp[3] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 static const size_t kSmemCap = 220 * 1024;
@@ -891,9 +1104,28 @@ template <> bool slab64_launch<float>(const LatticeDev& L, const MatvecArgs<floa
     return true;
 }
 
+template <typename Rl> static bool slab128_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st);
+template <> bool slab128_launch<double>(const LatticeDev&, const MatvecArgs<double>&, bool, cudaStream_t) { return false; }
+template <> bool slab128_launch<float>(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
+    if (L.My != 128 || L.Mz != 128) return false;
+    dim3 grid(L.Nx, a.S * 3);
+    count_launch();
+    const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
+    const size_t sm = sizeof(Slab128Smem);
+    if (L.Ny == 64 && L.Nz == 64) {
+        if (!inv) k_slab_fwd128<true><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv128<true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    } else {
+        if (!inv) k_slab_fwd128<false><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv128<false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    }
+    return true;
+}
+
 template <typename Rl> static void slab_launch_any(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, int cw,
                                                    cudaStream_t st) {
     if (slab64_launch<Rl>(L, a, inv, st)) return;
+    if (slab128_launch<Rl>(L, a, inv, st)) return;
     if (cw == 32) slab_launch<Rl, 32>(L, a, inv, st);
     else if (cw == 16) slab_launch<Rl, 16>(L, a, inv, st);
     else slab_launch<Rl, 8>(L, a, inv, st);
@@ -996,6 +1228,10 @@ void prepare_kernels() {
     allow_smem(k_slab_fwd64<false>);
     allow_smem(k_slab_inv64<true>);
     allow_smem(k_slab_inv64<false>);
+    allow_smem(k_slab_fwd128<true>);
+    allow_smem(k_slab_fwd128<false>);
+    allow_smem(k_slab_inv128<true>);
+    allow_smem(k_slab_inv128<false>);
     prepare_far_kernels();
 }
 
