@@ -79,3 +79,38 @@ def scaled_kinetic_energy(ekin_keV: float, eps_h: float) -> float:
     e0 = ME_C2_KEV
     e = ekin_keV
     return e0 * ((e + e0) / np.sqrt(e0 ** 2 - (eps_h - 1.0) * e * (2.0 * e0 + e)) - 1.0)
+
+
+def vacuum_equivalent(ekin_keV: float, eps_h: float, energy_eV: float, length_rule: bool = False,
+                      ultrarelativistic: bool = False) -> dict:
+    """Sec. 2.7: a vacuum problem whose probabilities give those of a particle
+    in a real host eps_h.  Eq. 43-44 rescale the indices by eta and every
+    length by xi (k by 1/xi); then omega -> xi eta omega, v -> eta v and
+    P -> P / xi.  With eta = m_h the host becomes vacuum:
+      * xi = 1 (Eq. 45): same lattice, loss energy m_h hbar omega;
+      * xi = 1/m_h (Eq. 46): lengths times m_h, same loss energy, P / m_h.
+    The particle permittivity becomes eps_p(omega) / eps_h (m_p -> m_p / eta,
+    taken at the original frequency) and the kinetic energy follows Eq. 47.
+    Both need beta_h < 1.  For beta_h > 1, Eq. S16 (approximate, from the
+    quasi-static field of Eq. S15) sets v = c in the vacuum problem and
+    divides its probabilities by beta_h^2.
+    Returns ekin_keV (inf for v = c), energy_eV, length_scale, eps_p_scale
+    and p_scale with P_host = p_scale * P_vacuum."""
+    if not (eps_h > 0 and ekin_keV > 0 and energy_eV > 0):
+        raise ValueError("vacuum equivalence needs a real positive eps_h")
+    m_h = float(np.sqrt(eps_h))
+    beta_h = electron_speed(ekin_keV) * m_h / C_LIGHT
+    eta = m_h
+    xi = 1.0 / m_h if length_rule else 1.0
+    out = {"energy_eV": xi * eta * energy_eV, "length_scale": 1.0 / xi, "eps_p_scale": 1.0 / eta ** 2,
+           "p_scale": xi}
+    if ultrarelativistic:
+        if not beta_h > 1.0:
+            raise ValueError("Eq. S16 applies above the Cherenkov threshold")
+        out["ekin_keV"] = float("inf")
+        out["p_scale"] = xi / beta_h ** 2
+    else:
+        if not beta_h < 1.0:
+            raise ValueError("no vacuum equivalent at or above the Cherenkov threshold (v m_h >= c)")
+        out["ekin_keV"] = float(scaled_kinetic_energy(ekin_keV, eps_h))
+    return out

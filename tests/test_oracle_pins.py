@@ -291,6 +291,62 @@ def test_scale_rule_eq45_vacuum_emulation():
         assert vac[key] == pytest.approx(host[key], rel=1e-10), key
 
 
+def test_vacuum_equivalent_eq45_eq46_reproduce_host_probabilities():
+    """Sec. 2.7: the vacuum problems of Eq. 45 (same lattice, loss energy
+    m_h hbar omega) and Eq. 46 (lengths times m_h, probabilities / m_h), with
+    the kinetic energy of Eq. 47, give the host problem's probabilities, by
+    dense solves of both problems."""
+    n, _, _, d, occ = _small_sphere()
+    eps_h, e, ek, beam = 2.1025, 2.3, 100.0, (12.0, 3.0)
+    eps_p = I.drude(e)
+    host = run.solve_point(n, n, n, d, occ, e, [eps_p], eps_h, beam, ekin_keV=ek)
+    for length_rule in (False, True):
+        m = physics.vacuum_equivalent(ek, eps_h, e, length_rule=length_rule)
+        s = m["length_scale"]
+        assert s == pytest.approx(1.45 if length_rule else 1.0, rel=1e-15)
+        vac = run.solve_point(n, n, n, d * s, occ, m["energy_eV"], [eps_p * m["eps_p_scale"]], 1.0,
+                              (beam[0] * s, beam[1] * s), ekin_keV=m["ekin_keV"])
+        assert vac["point"].beta_h.real < 1
+        for key in ("P_EELS", "P_CL", "P_ext", "P_abs"):
+            assert m["p_scale"] * vac[key] == pytest.approx(host[key], rel=1e-10), (length_rule, key)
+    with pytest.raises(ValueError):
+        physics.vacuum_equivalent(200.0, 4.0, 2.0)                      # beta_h > 1: no exact vacuum map
+    with pytest.raises(ValueError):
+        physics.vacuum_equivalent(100.0, 2.1025, 2.0, ultrarelativistic=True)
+    with pytest.raises(ValueError):
+        physics.vacuum_equivalent(100.0, -1.0, 2.0)
+
+
+def test_vacuum_equivalent_s16_is_the_quasi_static_limit_of_eq25():
+    """Eq. S16: above the threshold the vacuum problem runs at v = c and its
+    probabilities are divided by beta_h^2.  Pinned on the incident field of
+    Eq. 25 itself: near the trajectory (w b / (|gamma_h| v) -> 0, Eq. S15)
+    (xi eta)^2 |E_host|^2 / |E_vacuum(v -> c)|^2 tends to p_scale / xi, with
+    an error of order a^2 |ln a|, a = w b / (|gamma_h| v)."""
+    eps_h, ek, e, m_h = 4.0, 200.0, 2.0, 2.0
+    v = physics.electron_speed(ek)
+    _, gam = physics.beta_gamma_h(v, m_h)
+    vc = physics.electron_speed(1e8)                 # 1 - v/c ~ 1e-11
+    _, gc = physics.beta_gamma_h(vc, 1.0)
+    w = physics.omega_of(e)
+    for length_rule in (False, True):
+        m = physics.vacuum_equivalent(ek, eps_h, e, length_rule=length_rule, ultrarelativistic=True)
+        assert m["ekin_keV"] == float("inf")
+        xi = 1.0 / m["length_scale"]
+        w2 = physics.omega_of(m["energy_eV"])
+        prev = None
+        for b in (2e-9, 1e-9, 0.5e-9, 0.25e-9):
+            r = np.array([[b, 0.0, 0.0], [0.6 * b, 0.8 * b, 0.0]])
+            eh = field.incident_field(r, w, v, m_h, gam, 0.0, 0.0)
+            ec = field.incident_field(r * m["length_scale"], w2, vc, 1.0, gc, 0.0, 0.0)
+            ratio = (xi * m_h) ** 2 * np.sum(abs(eh) ** 2) / np.sum(abs(ec) ** 2)
+            err = abs(ratio / (m["p_scale"] / xi) - 1.0)
+            a = w * b / (abs(gam) * v)
+            assert err < 10 * a * a * abs(np.log(a)), (length_rule, b)
+            assert prev is None or err < prev
+            prev = err
+
+
 def test_scale_rule_eq43_44_general_cherenkov():
     n, _, _, d, occ = _small_sphere(6, 30.0)
     eta, xi = 1.3, 0.7
