@@ -317,6 +317,34 @@ int eels_cl_total(int n, const double* p_eels, const double* p_ext, const double
  * host, Sec. 2.5): EELS_E_INVALID_ARG otherwise. */
 int eels_frank_tamm(double ekin_keV, eels_c128 eps_h, double* dp_dz);
 
+/* A vacuum problem equivalent to a particle in a real host (Sec. 2.7).
+ * Eq. 43-44 scale every refractive index by 1/eta and every length by 1/xi;
+ * with eta = m_h = sqrt(eps_h) the host becomes vacuum.  Rules (flags):
+ *   EELS_SCALE_ENERGY  Eq. 45: xi = 1 -- same lattice and beams, loss
+ *                      energy m_h * energy_eV, same probabilities;
+ *   EELS_SCALE_LENGTH  Eq. 46: xi = 1/m_h -- lattice spacing and beam
+ *                      offsets times m_h, same loss energy, probabilities
+ *                      of the vacuum problem divided by m_h;
+ *   | EELS_SCALE_ULTRAREL  Eq. S16, only above the Cherenkov threshold
+ *                      (beta_h > 1), approximate (quasi-static field,
+ *                      Eq. S15): the vacuum problem runs at v = c and its
+ *                      probabilities are further divided by beta_h^2.
+ * Outputs (host struct): ekin_keV, the vacuum kinetic energy with speed m_h v
+ * (Eq. 47), or +inf for v = c (a vacuum solve then takes a kinetic energy
+ * large enough that w b / (gamma v) is negligible); energy_eV, the loss
+ * energy of the vacuum problem; length_scale, the factor on d_nm and beam
+ * offsets; eps_p_scale = 1/eps_h, the factor on every particle permittivity
+ * taken at the ORIGINAL loss energy; p_scale, with P_host = p_scale *
+ * P_vacuum for P_EELS, P_CL, P_ext and P_abs.  eps_h is real (eta must be,
+ * Eq. 43).  EELS_E_INVALID_ARG for eps_h <= 0, ekin_keV <= 0, energy_eV <= 0,
+ * unknown flags, or a rule on the wrong side of the threshold (the exact
+ * rules need beta_h < 1, Eq. S16 beta_h > 1). */
+enum { EELS_SCALE_ENERGY = 0, EELS_SCALE_LENGTH = 1, EELS_SCALE_ULTRAREL = 2 };
+typedef struct {
+    double ekin_keV, energy_eV, length_scale, eps_p_scale, p_scale;
+} eels_vacuum_map;
+int eels_vacuum_equivalent(int rule, double ekin_keV, double eps_h, double energy_eV, eels_vacuum_map* out);
+
 /* Extrapolation of one result to zero dipole size (Sec. 3.2): values[i]
  * computed with dipole size d[i] (n >= 3 points, any length unit, d > 0)
  * are fitted with a0 + a1 d + a2 d^2 by least squares with weights d^-6

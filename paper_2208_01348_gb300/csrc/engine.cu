@@ -23,6 +23,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <memory>
 #include <string>
@@ -1320,6 +1321,30 @@ int eels_frank_tamm(double ekin_keV, eels_c128 eps_h, double* dp_dz) {
     const double b2 = v * v * eps_h.re / (kC * kC);   // beta_h^2
     // (2/pi) (dW0/dz) / (hbar^2 w) e with dW0/dz = (mu0/8) e^2 w (1 - 1/beta_h^2), mu0 = 1/(eps0 c^2)
     *dp_dz = b2 <= 1.0 ? 0.0 : kE * kE * (1.0 - 1.0 / b2) / (4.0 * kPi * kEps0 * kC * kC * kHbar * kHbar) * kE;
+    return EELS_OK;
+}
+
+int eels_vacuum_equivalent(int rule, double ekin_keV, double eps_h, double energy_eV, eels_vacuum_map* out) {
+    if (!out || !(ekin_keV > 0) || !(eps_h > 0) || !(energy_eV > 0) ||
+        (rule & ~(EELS_SCALE_LENGTH | EELS_SCALE_ULTRAREL)))
+        return EELS_E_INVALID_ARG;
+    const double m_h = std::sqrt(eps_h), beta_h = electron_speed(ekin_keV) * m_h / kC;
+    const double eta = m_h, xi = (rule & EELS_SCALE_LENGTH) ? 1.0 / m_h : 1.0;
+    eels_vacuum_map m;
+    m.energy_eV = xi * eta * energy_eV;    // omega -> xi eta omega (Eq. 44)
+    m.length_scale = 1.0 / xi;             // r -> r / xi (Eq. 43)
+    m.eps_p_scale = 1.0 / (eta * eta);     // m_p -> m_p / eta
+    m.p_scale = xi;                        // P -> P / xi (Eq. 44), inverted
+    if (rule & EELS_SCALE_ULTRAREL) {
+        if (!(beta_h > 1.0)) return EELS_E_INVALID_ARG;
+        m.ekin_keV = std::numeric_limits<double>::infinity();
+        m.p_scale = xi / (beta_h * beta_h);   // Eq. S16: P -> beta_h^2 P at v = c, inverted
+    } else {
+        if (!(beta_h < 1.0)) return EELS_E_INVALID_ARG;
+        // the kinetic energy of speed m_h v (Eq. 47 is its closed form)
+        m.ekin_keV = kMeC2keV * (1.0 / std::sqrt((1.0 - beta_h) * (1.0 + beta_h)) - 1.0);
+    }
+    *out = m;
     return EELS_OK;
 }
 

@@ -69,6 +69,11 @@ class eels_job_info(C.Structure):
                 ("t_end", C.c_double), ("footprint", C.c_size_t), ("n_points", C.c_int)]
 
 
+class eels_vacuum_map(C.Structure):
+    _fields_ = [("ekin_keV", C.c_double), ("energy_eV", C.c_double), ("length_scale", C.c_double),
+                ("eps_p_scale", C.c_double), ("p_scale", C.c_double)]
+
+
 EELS_JOB_QUEUED, EELS_JOB_RUNNING, EELS_JOB_DONE, EELS_JOB_FAILED = 0, 1, 2, 3
 EELS_SERVER_DRYRUN = 1
 
@@ -102,6 +107,7 @@ _sig = {
     "eels_cl_total": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
     "eels_frank_tamm": (C.c_int, [C.c_double, eels_c128, _dp]),
     "eels_extrapolate": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
+    "eels_vacuum_equivalent": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(eels_vacuum_map)]),
     "eels_tile_widths": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
@@ -374,6 +380,20 @@ def eels_extrapolate(d, values):
     v0, ci = C.c_double(), C.c_double()
     _check(_lib.eels_extrapolate(len(dd_), _dptr(dd_), _dptr(vv), C.byref(v0), C.byref(ci)))
     return v0.value, ci.value
+
+
+EELS_SCALE_ENERGY, EELS_SCALE_LENGTH, EELS_SCALE_ULTRAREL = 0, 1, 2
+
+
+def eels_vacuum_equivalent(ekin_keV: float, eps_h: float, energy_eV: float, rule: int = EELS_SCALE_ENERGY) -> dict:
+    """Vacuum problem equivalent to a particle in the real host eps_h (Sec. 2.7:
+    Eq. 45 / 46, or with EELS_SCALE_ULTRAREL the approximate Eq. S16 above the
+    threshold).  Keys: ekin_keV (inf for v = c), energy_eV, length_scale,
+    eps_p_scale (applied to eps_p at the original energy), p_scale
+    (P_host = p_scale * P_vacuum)."""
+    m = eels_vacuum_map()
+    _check(_lib.eels_vacuum_equivalent(int(rule), float(ekin_keV), float(eps_h), float(energy_eV), C.byref(m)))
+    return {f: getattr(m, f) for f, _ in eels_vacuum_map._fields_}
 
 
 def eels_tile_widths(ctx):

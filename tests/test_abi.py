@@ -118,3 +118,34 @@ def test_extrapolation_utility_matches_oracle():
         assert ci == pytest.approx(rci, rel=1e-7, abs=1e-9)   # noiseless: both are rounding-level
     with pytest.raises(dd.EelsError):
         dd.eels_extrapolate([1.0, 2.0], [1.0, 2.0])
+
+
+def test_vacuum_equivalent_utility_matches_oracle():
+    """eels_vacuum_equivalent (Sec. 2.7, Eq. 45-47, Eq. S16) against the
+    oracle's map; the library takes the kinetic energy of speed m_h v directly,
+    the oracle by Eq. 47, so the two routes check each other."""
+    import math
+    from oracle import physics
+    from paper_2208_01348_gb300 import eelsdda as dd
+    cases = [(100.0, 2.1025, 2.3), (60.0, 1.69, 1.1), (300.0, 1.21, 3.9), (200.0, 1.44, 2.0)]
+    for ek, eps_h, e in cases:
+        for rule in (dd.EELS_SCALE_ENERGY, dd.EELS_SCALE_LENGTH):
+            got = dd.eels_vacuum_equivalent(ek, eps_h, e, rule)
+            ref = physics.vacuum_equivalent(ek, eps_h, e, length_rule=rule == dd.EELS_SCALE_LENGTH)
+            for key in ("ekin_keV", "energy_eV", "length_scale", "eps_p_scale", "p_scale"):
+                assert got[key] == pytest.approx(ref[key], rel=1e-12), (ek, eps_h, rule, key)
+            with pytest.raises(dd.EelsError):
+                dd.eels_vacuum_equivalent(ek, eps_h, e, rule | dd.EELS_SCALE_ULTRAREL)
+    for ek, eps_h, e in ((200.0, 4.0, 2.0), (100.0, 6.25, 3.0)):
+        for rule in (dd.EELS_SCALE_ENERGY, dd.EELS_SCALE_LENGTH):
+            got = dd.eels_vacuum_equivalent(ek, eps_h, e, rule | dd.EELS_SCALE_ULTRAREL)
+            ref = physics.vacuum_equivalent(ek, eps_h, e, length_rule=rule == dd.EELS_SCALE_LENGTH,
+                                            ultrarelativistic=True)
+            assert math.isinf(got["ekin_keV"]) and math.isinf(ref["ekin_keV"])
+            for key in ("energy_eV", "length_scale", "eps_p_scale", "p_scale"):
+                assert got[key] == pytest.approx(ref[key], rel=1e-12), (ek, eps_h, rule, key)
+            with pytest.raises(dd.EelsError):
+                dd.eels_vacuum_equivalent(ek, eps_h, e, rule)
+    for bad in ((0.0, 2.0, 2.0, 0), (100.0, 0.0, 2.0, 0), (100.0, 2.0, -1.0, 0), (100.0, 2.0, 2.0, 4)):
+        with pytest.raises(dd.EelsError):
+            dd.eels_vacuum_equivalent(bad[0], bad[1], bad[2], bad[3])

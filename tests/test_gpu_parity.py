@@ -363,3 +363,36 @@ def test_oblique_electron_solves_match_lu_and_rotations_agree(dd, ctx):
     with pytest.raises(dd.EelsError) as e:
         dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, [[0.0, 1.0]])
     assert e.value.code == dd.EELS_E_BEAM_INSIDE
+
+
+def test_vacuum_equivalent_problems_reproduce_host_probabilities(dd, ctx):
+    """Sec. 2.7 through the library: a gold sphere in glass (eps_h = 2.1025)
+    and the vacuum problems eels_vacuum_equivalent gives for it (Eq. 45:
+    loss energy times m_h; Eq. 46: lengths times m_h, probabilities / m_h)
+    give the same probabilities; the host solve itself matches the oracle's
+    LU solve."""
+    w = I.config_small_sphere()
+    g = w.grid
+    eps_h, ek = 2.1025, 100.0
+    energies = np.array([1.9, 2.4])
+    eps_p = np.array([[I.drude(e)] for e in energies])
+    beam = np.array([[15.0, 2.0]])
+    opts = dict(precision=dd.EELS_FP64, eps_it=1e-12)
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    host = dd.eels_solve(ctx, dd.eels_default_opts(ekin_keV=ek, **opts), energies, eps_p,
+                         np.full(len(energies), eps_h, dtype=complex), beam)
+    assert host.converged.all()
+    ref = run.solve_point(g.nx, g.ny, g.nz, g.d_nm, g.occ, energies[1], eps_p[1], eps_h, beam[0], ekin_keV=ek)
+    for key, got in (("P_EELS", host.p_eels), ("P_CL", host.p_cl)):
+        assert abs(got[1, 0] - ref[key]) <= 1e-10 * abs(ref[key]), key
+    for rule in (dd.EELS_SCALE_ENERGY, dd.EELS_SCALE_LENGTH):
+        maps = [dd.eels_vacuum_equivalent(ek, eps_h, e, rule) for e in energies]
+        s = maps[0]["length_scale"]
+        dd.eels_set_grid(ctx, g.occ, g.d_nm * s)
+        vac = dd.eels_solve(ctx, dd.eels_default_opts(ekin_keV=maps[0]["ekin_keV"], **opts),
+                            np.array([m["energy_eV"] for m in maps]), eps_p * maps[0]["eps_p_scale"],
+                            np.ones(len(energies), dtype=complex), beam * s)
+        assert vac.converged.all()
+        for a, b in ((vac.p_eels, host.p_eels), (vac.p_cl, host.p_cl), (vac.p_ext, host.p_ext),
+                     (vac.p_abs, host.p_abs)):
+            assert np.allclose(maps[0]["p_scale"] * a, b, rtol=1e-9, atol=0), rule
