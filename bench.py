@@ -300,7 +300,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-concurrency", type=int, default=8)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--solver", default="qmr", choices=["qmr", "bicgstab"])
+    ap.add_argument("--solver", default="qmr2", choices=["qmr2", "qmr", "bicgstab"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=5,
                     help="energies of the plain FP64 single-system comparison (0: skip)")
@@ -347,7 +347,7 @@ def main():
     g = w.grid
     prec = dd.EELS_MIXED if args.precision == "mixed" else dd.EELS_FP64
     opts = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=prec, eps_it=1e-8, eps_inner=1e-5, n_dir=w.n_dir,
-                                solver=dd.EELS_QMR if args.solver == "qmr" else dd.EELS_BICGSTAB)
+                                solver={"qmr2": dd.EELS_QMR2, "qmr": dd.EELS_QMR, "bicgstab": dd.EELS_BICGSTAB}[args.solver])
     dd.eels_set_grid(ctx, g.occ, g.d_nm)
 
     def step():

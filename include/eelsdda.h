@@ -61,7 +61,11 @@ enum {
 };
 
 enum { EELS_FP64 = 0, EELS_MIXED = 1 };          /* precision of the Krylov iterations */
-enum { EELS_QMR = 0, EELS_BICGSTAB = 1 };       /* complex-symmetric Krylov solver */
+/* Krylov solver: EELS_QMR2 = QMR from coupled two-term recurrences (the variant
+ * the paper found fastest, Sec. S5; the default), EELS_QMR = QMR from the
+ * three-term Lanczos recurrence (both for complex-symmetric matrices),
+ * EELS_BICGSTAB = BiCGStab with the conjugated inner product. */
+enum { EELS_QMR = 0, EELS_BICGSTAB = 1, EELS_QMR2 = 2 };
 
 typedef struct { double re, im; } eels_c128;
 
@@ -78,7 +82,7 @@ typedef struct { double x0_nm, y0_nm; } eels_beam;   /* electron along +z, z0 = 
 typedef struct {
     double ekin_keV;         /* electron kinetic energy */
     int precision;           /* EELS_FP64: FP64 Krylov; EELS_MIXED: FP32 Krylov + FP64 refinement */
-    int solver;              /* EELS_QMR or EELS_BICGSTAB */
+    int solver;              /* EELS_QMR2, EELS_QMR or EELS_BICGSTAB */
     double eps_it;           /* target relative residual ||b - A x|| / ||b|| (FP64) of the Jacobi-scaled system */
     double eps_inner;        /* EELS_MIXED: relative residual target of each FP32 inner solve */
     int max_iter;            /* Krylov iterations per inner solve (and in total for EELS_FP64) */
@@ -101,7 +105,7 @@ typedef struct {
     int converged;           /* 1 if residual <= eps_it */
 } eels_point_stats;
 
-/* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR, eps_it 1e-8,
+/* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR2, eps_it 1e-8,
  * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 1000
  * (FP32 Lanczos recurrences lose biorthogonality on hard systems; restarting
  * every 1000 iterations from the FP64 residual keeps the iteration count

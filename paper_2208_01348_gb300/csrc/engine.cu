@@ -542,6 +542,7 @@ KrylovArgs<Rl> krylov_args(eels_ctx* c, int S, const eels_opts* o, double eps) {
     k.W = c->kv[5].as<cx<Rl>>(); k.X = c->kv[6].as<cx<Rl>>();
     k.part_a = c->part_a.as<double>(); k.part_b = c->part_b.as<double>();
     k.qmr = c->qmr.as<QmrState>();
+    k.qmr2 = c->qmr.as<Qmr2State>();
     // BiCGStab roles in the same seven buffers (the rhs arrives in kv[1], the iterate is kv[6])
     k.R = c->kv[1].as<cx<Rl>>(); k.Rh = c->kv[0].as<cx<Rl>>(); k.Pb = c->kv[2].as<cx<Rl>>();
     k.Vb = c->kv[3].as<cx<Rl>>(); k.Tb = c->kv[4].as<cx<Rl>>(); k.Sb = k.R;
@@ -577,11 +578,12 @@ template <typename Rl>
 int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
     cudaStream_t st = c->stream;
     KrylovArgs<Rl> k = krylov_args<Rl>(c, S, o, eps);
-    const bool bicg = o->solver == EELS_BICGSTAB;
-    // the three-pass matvec also returns the per-slab partial sums of v^T (A v)
+    const bool bicg = o->solver == EELS_BICGSTAB, qmr2 = o->solver == EELS_QMR2;
+    // the three-pass matvec also returns the per-slab partial sums of x^T (A x)
     const bool fused = !bicg && matvec_passes(c->L, sizeof(Rl) == 8) == 3;
     k.nblk_a = fused ? 3 * c->L.Nx : k.nblk;
     if (bicg) launch_bicg_init<Rl>(k, st);
+    else if (qmr2) launch_qmr2_init<Rl>(k, st);
     else launch_qmr_init<Rl>(k, st);
     CK(cudaGetLastError());
     constexpr int CHUNK = 6;   // period of the QMR vector-slot rotation (2 and 3)
@@ -590,7 +592,7 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
                                     (const void*)(size_t)S, (const void*)(size_t)sizeof(Rl),
                                     (const void*)(size_t)inner_cap(o, sizeof(Rl) == 4), c->coef.p, c->diag.p, c->slot.p, c->qmr.p,
                                     c->part_a.p, c->part_b.p, c->active.p, c->upd.p, c->counters.p, c->eps_sys.p,
-                                    c->cellmap.p, c->bicg.p, (const void*)(size_t)bicg};
+                                    c->cellmap.p, c->bicg.p, (const void*)(size_t)o->solver};
     // eps is read inside the step kernel from the kernel argument: make it part of the key
     double epsv = eps;
     const void* ek;
@@ -607,6 +609,13 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
                 launch_bicg_stage1<Rl>(k, st);
                 launch_matvec<Rl>(c->L, mv_args<Rl>(c, S, k.R, k.Tb, dr_of<Rl>(c), k.active, true), st);
                 launch_bicg_stage2<Rl>(k, st);
+                continue;
+            }
+            if (qmr2) {
+                MatvecArgs<Rl> a = mv_args<Rl>(c, S, k.P[0], k.W, dr_of<Rl>(c), k.active, true);
+                a.dot_part = fused ? k.part_a : nullptr;
+                launch_matvec<Rl>(c->L, a, st);
+                launch_qmr2_post_matvec<Rl>(k, fused, st);
                 continue;
             }
             MatvecArgs<Rl> a = mv_args<Rl>(c, S, k.V[n & 1], k.W, dr_of<Rl>(c), k.active, true);
@@ -666,6 +675,7 @@ int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::v
     const double eps_floor = (sizeof(Rl) == 4) ? std::max(o->eps_inner, 1e-7) : 1e-15;
     const double safety = (sizeof(Rl) == 4) ? 0.3 : 0.5;
     std::vector<QmrState> qh(S);
+    std::vector<Qmr2State> q2h(S);
     std::vector<BicgState> bh(S);
     std::vector<int> outer_h(S), slow_rounds(S, 0), stalled(S, 0);
     std::vector<double> res_h(S, 1.0), res_prev(S, 1.0);
@@ -707,6 +717,8 @@ int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::v
         inner_solve<Rl>(c, S, o, eps_floor);
         if (o->solver == EELS_BICGSTAB) {
             CK(cudaMemcpyAsync(bh.data(), c->bicg.p, S * sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+        } else if (o->solver == EELS_QMR2) {
+            CK(cudaMemcpyAsync(q2h.data(), c->qmr.p, S * sizeof(Qmr2State), cudaMemcpyDeviceToHost, st));
         } else {
             CK(cudaMemcpyAsync(qh.data(), c->qmr.p, S * sizeof(QmrState), cudaMemcpyDeviceToHost, st));
         }
@@ -722,7 +734,8 @@ int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::v
         CK(cudaStreamSynchronize(st));
         for (int s = 0; s < S; ++s)
             if (outer_h[s]) {
-                iters[s] += o->solver == EELS_BICGSTAB ? bh[s].iters : qh[s].iters;
+                iters[s] += o->solver == EELS_BICGSTAB ? bh[s].iters
+                                                       : o->solver == EELS_QMR2 ? q2h[s].iters : qh[s].iters;
                 refin[s] += 1;
             }
     }
@@ -730,13 +743,15 @@ int refine_rounds(eels_ctx* c, int S, const eels_opts* o, int max_rounds, std::v
 }
 
 // FP64 refinement of a batch.  EELS_MIXED: FP32 inner solves restarted
-// every inner_max_iter iterations.  With QMR, two rounds of QMR (most
-// systems of a spectrum converge in them), then the systems left continue
-// with FP32 BiCGStab for up to 30 rounds: on the hard systems restarted QMR
-// gains little per round, and its complex-symmetric Lanczos process can stall
-// or break down on a residual whose unconjugated square r^T r is small,
-// where BiCGStab, with its conjugated inner product, does not (on the
-// 200-energy spectrum: 1.85 s per step against 2.49 s with 30 QMR rounds).
+// every inner_max_iter iterations.  With two-term QMR, up to 30 rounds; a
+// system whose residual falls by less than 2x in two successive rounds
+// leaves them for FP32 BiCGStab rounds (the complex-symmetric Lanczos process
+// can stall or break down on a residual whose unconjugated square r^T r is
+// small, where BiCGStab, with its conjugated inner product, does not).  With
+// three-term QMR, whose FP32 recurrences lose biorthogonality much sooner,
+// only two QMR rounds (most systems of a spectrum converge in them), then
+// every system left goes to FP32 BiCGStab (on the 200-energy spectrum:
+// 1.85 s per step against 2.49 s with 30 three-term QMR rounds).
 // Systems still above eps_it finish with FP64 inner solves (BiCGStab after
 // FP32 rounds, for the same reason).  Lattices whose padded FFT grid has at
 // most 65,536 points (40^3) go straight to FP64 inner solves with the chosen
@@ -755,7 +770,7 @@ void refine_batch(eels_ctx* c, int S, const eels_opts* o, bool fp64, std::vector
     ob.solver = EELS_BICGSTAB;
     if (fp32_rounds) {
         left = refine_rounds<float>(c, S, o, o->solver == EELS_QMR ? 2 : 30, iters, refin);
-        if (left > 0 && o->solver == EELS_QMR) left = refine_rounds<float>(c, S, &ob, 30, iters, refin);
+        if (left > 0 && o->solver != EELS_BICGSTAB) left = refine_rounds<float>(c, S, &ob, 30, iters, refin);
     }
     if (left > 0) {
         const size_t kvec64 = (size_t)S * 3 * c->N * sizeof(double2);
@@ -774,7 +789,8 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         throw Fail{EELS_E_INVALID_ARG, "solve: NULL input or non-positive counts"};
     if (n_mat < c->max_mat || n_mat > EELS_MAX_MAT) throw Fail{EELS_E_INVALID_ARG, "n_mat does not cover the grid materials"};
     if (o->precision != EELS_FP64 && o->precision != EELS_MIXED) throw Fail{EELS_E_INVALID_ARG, "unknown precision"};
-    if (o->solver != EELS_QMR && o->solver != EELS_BICGSTAB) throw Fail{EELS_E_INVALID_ARG, "unknown solver"};
+    if (o->solver != EELS_QMR && o->solver != EELS_BICGSTAB && o->solver != EELS_QMR2)
+        throw Fail{EELS_E_INVALID_ARG, "unknown solver"};
     if (!(o->eps_it > 0) || o->max_iter <= 0) throw Fail{EELS_E_INVALID_ARG, "eps_it and max_iter must be positive"};
     if (p_cl && o->n_dir <= 0) throw Fail{EELS_E_INVALID_ARG, "p_cl requested with n_dir = 0"};
     const BeamFrame frame = beam_frame(o->beam_dir);
@@ -986,7 +1002,7 @@ void eels_default_opts(eels_opts* o) {
     if (!o) return;
     o->ekin_keV = 100.0;
     o->precision = EELS_MIXED;
-    o->solver = EELS_QMR;
+    o->solver = EELS_QMR2;
     o->eps_it = 1e-8;
     o->eps_inner = 1e-5;
     o->max_iter = 20000;

@@ -303,6 +303,223 @@ template void launch_qmr_init<double>(const KrylovArgs<double>&, cudaStream_t);
 template void launch_qmr_post_matvec<float>(const KrylovArgs<float>&, int, bool, cudaStream_t);
 template void launch_qmr_post_matvec<double>(const KrylovArgs<double>&, int, bool, cudaStream_t);
 
+// ------------------------------------------------------------------ QMR2
+// QMR from coupled two-term recurrences (Freund & Nachtigal, SIAM J. Sci.
+// Comput. 15 (1994) 313), the variant the paper found slightly faster than
+// the three-term one (Sec. S5).  With A = A^T the left Lanczos sequence
+// equals the right one, so an iteration costs one matvec.  Starting from
+// v_1 = b / rho_1, p_1 = v_1, d_0 = 0, gamma_0 = 1, eta_0 = -1, tau_0 = ||b||:
+//   eps_n = p_n^T (A p_n),  beta_n = eps_n / delta_n,
+//   v~ = A p_n - beta_n v_n,  rho_{n+1} = ||v~||,  delta_{n+1} = v~^T v~ / rho_{n+1}^2,
+//   theta_n = rho_{n+1} / (gamma_{n-1} |beta_n|),  gamma_n = (1 + theta_n^2)^(-1/2),
+//   eta_n = -eta_{n-1} rho_n gamma_n^2 / (beta_n gamma_{n-1}^2),
+//   d_n = eta_n p_n + (theta_{n-1} gamma_n)^2 d_{n-1},  x_n = x_{n-1} + d_n,
+//   v_{n+1} = v~ / rho_{n+1},  p_{n+1} = v_{n+1} - (rho_{n+1} delta_{n+1} / eps_n) p_n,
+// with the quasi-residual norm tau_n = tau_{n-1} theta_n gamma_n (the same
+// quantity the three-term form minimises).  In exact arithmetic the iterates
+// are those of the three-term form; in FP32 the two-term recurrences keep
+// the Lanczos vectors biorthogonal far longer.
+template <typename Rl>
+__global__ void k_qmr2_start(KrylovArgs<Rl> k) {
+    const int s = warp_system();
+    if (s >= k.S) return;
+    if (!k.active[s]) return;
+    double o[4];
+    warp_sum_parts(k.part_a, s, k.nblk, o);     // (b.b, |b|^2)
+    if (threadIdx.x & 31) return;
+    Qmr2State q;
+    const double rho = sqrt(o[2]);
+    q.bnorm = rho;
+    q.rho = rho;
+    q.tau = rho;
+    q.gam = 1.0;
+    q.th = 0.0;
+    q.cd = 0.0;
+    q.eta = make_double2(-1, 0);
+    q.cp = make_double2(0, 0);
+    q.iters = 0;
+    q.qres = 1.0;
+    q.status = 0;
+    q.delta = make_double2(1, 0);
+    q.inv_rho = 0.0;
+    if (rho > 0.0) {
+        q.inv_rho = 1.0 / rho;
+        q.delta = make_double2(o[0] / (rho * rho), o[1] / (rho * rho));
+        if (!(cabs_(q.delta) >= 1e-30)) q.status = 3;   // v_1^T v_1 = 0: no Lanczos step
+    } else {                        // zero right-hand side: x = 0 is exact
+        q.status = 1;
+        q.qres = 0.0;
+    }
+    if (q.status != 0) {
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+    }
+    k.qmr2[s] = q;
+}
+
+// v_1 = b / rho_1 (in V[1]); p_1 = v_1; d_0 = 0; x = 0
+template <typename Rl>
+__global__ void k_qmr2_scale(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y;
+    if (!k.active[s]) return;
+    const Rl ir = (Rl)k.qmr2[s].inv_rho;
+    const size_t off = (size_t)s * k.n3;
+    const cx<Rl> z = mk<cx<Rl>>(0.0, 0.0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x) {
+        const cx<Rl> v = ir * k.V[1][off + i];
+        k.V[1][off + i] = v;
+        k.P[0][off + i] = v;
+        k.P[1][off + i] = z;
+        k.X[off + i] = z;
+    }
+}
+
+// v~ = A p_n - beta_n v_n (into W), beta_n = eps_n / delta_n with eps_n from
+// part_a; partial sums of v~.v~ and |v~|^2 into part_b
+template <typename Rl>
+__global__ void k_qmr2_lanczos(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y, blk = blockIdx.x;
+    if (!k.active[s]) return;
+    __shared__ double2 sc;
+    if (threadIdx.x < 32) {
+        double o[4];
+        warp_sum_parts(k.part_a, s, k.nblk_a, o);
+        if (threadIdx.x == 0) sc = cdiv(make_double2(o[0], o[1]), k.qmr2[s].delta);
+    }
+    __syncthreads();
+    const cx<Rl> be = cvt<cx<Rl>>(sc);
+    const cx<Rl>* v = k.V[1];
+    const size_t off = (size_t)s * k.n3;
+    const int i0 = blk * RED_CHUNK, i1 = min(k.n3, i0 + RED_CHUNK);
+    Rl acc[4] = {0, 0, 0, 0};
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const cx<Rl> t = k.W[off + i] - be * v[off + i];
+        k.W[off + i] = t;
+        acc[0] += t.x * t.x - t.y * t.y;
+        acc[1] += 2 * t.x * t.y;
+        acc[2] += t.x * t.x + t.y * t.y;
+    }
+    block_sum<Rl, 4>(acc);
+    if (threadIdx.x == 0) {
+        double* p = k.part_b + ((size_t)s * k.nblk + blk) * 4;
+        p[0] = acc[0]; p[1] = acc[1]; p[2] = acc[2]; p[3] = 0.0;
+    }
+}
+
+template <typename Rl>
+__global__ void k_qmr2_step(KrylovArgs<Rl> k) {
+    const int s = warp_system();
+    if (s >= k.S) return;
+    const bool lead = (threadIdx.x & 31) == 0;
+    if (!k.active[s]) {
+        if (lead) k.upd[s] = 0;
+        return;
+    }
+    double oa[4], ob[4];
+    warp_sum_parts(k.part_a, s, k.nblk_a, oa);
+    warp_sum_parts(k.part_b, s, k.nblk, ob);
+    if (!lead) return;
+    Qmr2State q = k.qmr2[s];
+    const double2 eps = make_double2(oa[0], oa[1]);
+    const double2 beta = cdiv(eps, q.delta);
+    const double abeta = cabs_(beta);
+    const double rho_n = sqrt(ob[2]);
+    q.iters += 1;
+    int next = 1, upd = 1;
+    if (!(abeta > 0.0) || !(rho_n == rho_n)) {
+        // eps_n = 0 (or not finite): the coupled recurrences break down and
+        // this iteration's update is undefined; x keeps its previous value
+        q.status = 3; next = 0; upd = 0;
+    } else {
+        const double th = rho_n / (q.gam * abeta);
+        const double g = 1.0 / sqrt(1.0 + th * th);
+        const double f = q.rho * g * g / (q.gam * q.gam);
+        q.eta = -(f * cdiv(q.eta, beta));
+        q.cd = (q.th * g) * (q.th * g);
+        q.tau = q.tau * th * g;
+        q.qres = q.tau / q.bnorm;
+        q.th = th;
+        q.gam = g;
+        if (rho_n > 0.0) {
+            const double2 dn = make_double2(ob[0] / (rho_n * rho_n), ob[1] / (rho_n * rho_n));
+            q.cp = cdiv(rho_n * dn, eps);
+            q.inv_rho = 1.0 / rho_n;
+            q.rho = rho_n;
+            if (!(cabs_(dn) >= 1e-30)) { q.status = 3; next = 0; }
+            q.delta = dn;
+        } else {                    // invariant subspace reached: the update below is exact
+            q.cp = make_double2(0, 0);
+            q.inv_rho = 0.0;
+            q.status = 1; next = 0;
+        }
+        if (next && q.qres <= (k.eps_sys ? k.eps_sys[s] : k.eps)) { q.status = 1; next = 0; }
+        if (next && q.iters >= k.max_iter) { q.status = 2; next = 0; }
+        if (!(q.qres == q.qres) || !(q.eta.x == q.eta.x) || !(q.eta.y == q.eta.y)) {   // NaN guard
+            q.status = 3; next = 0; upd = 0;
+        }
+    }
+    k.qmr2[s] = q;
+    k.upd[s] = upd;
+    if (!next) {
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+    }
+}
+
+// d_n = eta_n p_n + cd d_{n-1}; x += d_n; v_{n+1} = v~ / rho_{n+1};
+// p_{n+1} = v_{n+1} - cp p_n
+template <typename Rl>
+__global__ void k_qmr2_update(KrylovArgs<Rl> k) {
+    const int s = blockIdx.y;
+    if (!k.upd[s]) return;
+    using C = cx<Rl>;
+    const Qmr2State& q = k.qmr2[s];
+    const C eta = cvt<C>(q.eta), cp = cvt<C>(q.cp);
+    const Rl cd = (Rl)q.cd, ir = (Rl)q.inv_rho;
+    const size_t off = (size_t)s * k.n3;
+    C* v = k.V[1];
+    C* p = k.P[0];
+    C* d = k.P[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n3; i += gridDim.x * blockDim.x) {
+        const C pn = p[off + i];
+        const C dn = eta * pn + cd * d[off + i];
+        d[off + i] = dn;
+        k.X[off + i] = k.X[off + i] + dn;
+        const C vn = ir * k.W[off + i];
+        v[off + i] = vn;
+        p[off + i] = vn - cp * pn;
+    }
+}
+
+template <typename Rl>
+void launch_qmr2_init(const KrylovArgs<Rl>& k, cudaStream_t st) {
+    count_launch();
+    k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.V[1], k.V[1], k.part_a, k.active);
+    count_launch();
+    k_qmr2_start<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
+    count_launch();
+    k_qmr2_scale<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
+}
+
+template <typename Rl>
+void launch_qmr2_post_matvec(const KrylovArgs<Rl>& k, bool dot_done, cudaStream_t st) {
+    if (!dot_done) {
+        count_launch();
+        k_dot<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k.n3, k.nblk, k.P[0], k.W, k.part_a, k.active);
+    }
+    count_launch();
+    k_qmr2_lanczos<Rl><<<dim3(k.nblk, k.S), RED_THREADS, 0, st>>>(k);
+    count_launch();
+    k_qmr2_step<Rl><<<warp_blocks(k.S), 128, 0, st>>>(k);
+    count_launch();
+    k_qmr2_update<Rl><<<vec_grid(k.n3, k.S), 256, 0, st>>>(k);
+}
+
+template void launch_qmr2_init<float>(const KrylovArgs<float>&, cudaStream_t);
+template void launch_qmr2_init<double>(const KrylovArgs<double>&, cudaStream_t);
+template void launch_qmr2_post_matvec<float>(const KrylovArgs<float>&, bool, cudaStream_t);
+template void launch_qmr2_post_matvec<double>(const KrylovArgs<double>&, bool, cudaStream_t);
+
 // ------------------------------------------------------------- BiCGStab
 // van der Vorst (SIAM J. Sci. Stat. Comput. 13 (1992) 631) for a general
 // complex matrix: shadow residual r^ = r0 and the conjugated inner product

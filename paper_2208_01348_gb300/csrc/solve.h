@@ -21,6 +21,23 @@ struct QmrState {
     int status;           // 0 running, 1 converged, 2 iteration limit, 3 breakdown
 };
 
+// Per-system scalars of QMR from coupled two-term recurrences (FP64).
+struct Qmr2State {
+    double2 delta;        // delta_n = v_n^T v_n (unconjugated)
+    double2 eta;          // d_n = eta_n p_n + cd d_{n-1}
+    double2 cp;           // p_{n+1} = v_{n+1} - cp p_n
+    double rho;           // rho_n = ||v~_n||
+    double gam, th;       // gamma_{n-1}, theta_{n-1}
+    double cd;            // (theta_{n-1} gamma_n)^2
+    double tau;           // quasi-residual norm tau_n
+    double inv_rho;       // 1 / rho_{n+1}: v_{n+1} = v~_{n+1} / rho_{n+1}
+    double bnorm;         // ||b||
+    double qres;          // tau_n / ||b||
+    int iters;
+    int status;           // 0 running, 1 converged, 2 iteration limit, 3 breakdown
+};
+static_assert(sizeof(Qmr2State) <= sizeof(QmrState), "Qmr2State shares the QmrState buffer");
+
 // BiCGStab per-system scalars (FP64).
 struct BicgState {
     double2 rho, alpha, omega, beta;
@@ -41,6 +58,7 @@ struct KrylovArgs {
     double* part_a;                // [S][nblk][4] block partial sums
     double* part_b;
     QmrState* qmr;
+    Qmr2State* qmr2;               // same memory as qmr (one solver runs at a time)
     BicgState* bicg;
     int* active;                   // [S] 1 while the system iterates
     int* upd;                      // [S] 1 if this iteration's vector update applies
@@ -57,6 +75,11 @@ constexpr int RED_CHUNK = 4096;    // vector entries per reduction block
 template <typename Rl> void launch_qmr_init(const KrylovArgs<Rl>& k, cudaStream_t st);
 // One QMR iteration n >= 1; the caller supplies the matvec (W = A V[n%2]).
 template <typename Rl> void launch_qmr_post_matvec(const KrylovArgs<Rl>& k, int n, bool dot_done, cudaStream_t st);
+// QMR from coupled two-term recurrences (Freund & Nachtigal 1994), complex
+// symmetric: rhs in V[1]; vector roles V[1] = v_n, P[0] = p_n (the matvec
+// input, W = A P[0]), P[1] = d_n, X.
+template <typename Rl> void launch_qmr2_init(const KrylovArgs<Rl>& k, cudaStream_t st);
+template <typename Rl> void launch_qmr2_post_matvec(const KrylovArgs<Rl>& k, bool dot_done, cudaStream_t st);
 // BiCGStab (van der Vorst 1992) with the shadow residual r^ = r0 and the
 // conjugated inner product (general complex form); rhs in R, X = 0.
 // Vector roles: R (residual; the rhs on entry, S = R - alpha V overwrites

@@ -34,6 +34,7 @@ EELS_FP64 = 0
 EELS_MIXED = 1
 EELS_QMR = 0
 EELS_BICGSTAB = 1
+EELS_QMR2 = 2
 
 
 class eels_c128(C.Structure):

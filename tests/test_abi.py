@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_default_opts(lib):
     o = lib.eels_default_opts()
-    assert o.precision == lib.EELS_MIXED and o.solver == lib.EELS_QMR
+    assert o.precision == lib.EELS_MIXED and o.solver == lib.EELS_QMR2
     assert o.eps_it == 1e-8 and o.eps_inner == 1e-5 and o.n_dir == 2562
 
 

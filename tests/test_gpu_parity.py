@@ -250,14 +250,16 @@ def test_invalid_inputs_raise(dd, ctx):
     assert e.value.code == dd.EELS_E_INVALID_ARG
 
 
+@pytest.mark.parametrize("solver", ["BICGSTAB", "QMR"])
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
-def test_bicgstab_matches_lu(dd, ctx, prec):
-    """The BiCGStab inner solver reaches the same solution as LU (Cherenkov
-    absorbing host replica, 3 energies, and the small gold sphere)."""
+def test_other_solvers_match_lu(dd, ctx, prec, solver):
+    """The BiCGStab and three-term QMR inner solvers reach the same solution
+    as LU (Cherenkov absorbing host replica, 3 energies, and the small gold
+    sphere); the default two-term QMR is covered by every other solve."""
     for w in (I.reduced(I.config_cherenkov(), 12 / 64, n_energy=3), I.config_small_sphere()):
         g = w.grid
         dd.eels_set_grid(ctx, g.occ, g.d_nm)
-        o = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=getattr(dd, "EELS_" + prec), solver=dd.EELS_BICGSTAB,
+        o = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=getattr(dd, "EELS_" + prec), solver=getattr(dd, "EELS_" + solver),
                                  eps_it=1e-12 if prec == "FP64" else 1e-8)
         res = dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, w.beams_nm, want_p=True)
         assert res.converged.all()
@@ -282,11 +284,12 @@ def test_async_solve_matches_blocking_solve(dd, ctx):
 
 
 
-def test_mixed_fp32_rounds_match_oracle_above_fp64_threshold(dd, ctx):
+@pytest.mark.parametrize("solver", ["QMR2", "QMR"])
+def test_mixed_fp32_rounds_match_oracle_above_fp64_threshold(dd, ctx, solver):
     """A lattice whose padded grid (32 x 32 x 72) is above the size where the
     mixed path switches to FP64 inner solves, so FP32 QMR rounds with FP64
-    refinement run; the oracle solves the same points with its own FFT
-    operator and GMRES."""
+    refinement run (two-term and three-term QMR); the oracle solves the same
+    points with its own FFT operator and GMRES."""
     nx, ny, nz, d_nm = 16, 16, 36, 1.5
     occ = I.box_occupancy(nx, ny, nz)
     dd.eels_set_grid(ctx, occ, d_nm)
@@ -295,7 +298,8 @@ def test_mixed_fp32_rounds_match_oracle_above_fp64_threshold(dd, ctx):
     eps_p = I.drude(e)[:, None]
     eps_h = np.full(2, 2.1025 + 0j)
     beam = np.array([[nx * d_nm / 2 + 6.0, 0.0]])
-    o = dd.eels_default_opts(ekin_keV=100.0, precision=dd.EELS_MIXED, eps_it=1e-8)
+    o = dd.eels_default_opts(ekin_keV=100.0, precision=dd.EELS_MIXED, eps_it=1e-8,
+                             solver=getattr(dd, "EELS_" + solver))
     res = dd.eels_solve(ctx, o, e, eps_p, eps_h, beam)
     assert res.converged.all()
     for ie in range(2):
