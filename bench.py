@@ -46,10 +46,12 @@ WORKLOADS = {
 CPU_SAMPLE = {"spectrum": (100, 0), "small": (0, 0), "cherenkov": (50, 0), "rod": (4, 0)}
 
 # ncu DRAM traffic (read + write bytes) of one matvec launch set, per system,
-# measured on the kernels whose sources hash to TRAFFIC_SRC_HASH; reported as
-# null when the kernel sources differ from the measured ones.
+# measured on the 64^3-FFT kernels of the spectrum workload whose sources hash
+# to TRAFFIC_SRC_HASH; reported as null for other workloads (other FFT sizes,
+# other kernels) and when the kernel sources differ from the measured ones.
 TRAFFIC_BYTES_PER_SYSTEM = 13_713_772       # profiles/fft_matvec_sphere32_64systems.md
 TRAFFIC_SRC_HASH = "730a9a2c5c0e6dec"
+TRAFFIC_WORKLOAD = "spectrum"
 
 
 def kernel_src_hash() -> str:
@@ -416,7 +418,8 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
     traffic = None
-    if TRAFFIC_BYTES_PER_SYSTEM is not None and TRAFFIC_SRC_HASH == kernel_src_hash():
+    if (TRAFFIC_BYTES_PER_SYSTEM is not None and args.workload == TRAFFIC_WORKLOAD
+            and TRAFFIC_SRC_HASH == kernel_src_hash()):
         traffic = TRAFFIC_BYTES_PER_SYSTEM * S
 
     # the plain FP64 path, one system per solve, on a sample of the energies
