@@ -35,20 +35,25 @@ def _dxi(n, x):
     return h + x * dh
 
 
-def mie_cross_sections(m_rel: complex, k: float, a: float, n_max=None):
-    x = k * a
+def mie_coefficients(m_rel: complex, x: float, n_max: int):
+    """Arrays a_n, b_n (n = 1..n_max) for size parameter x = k a."""
     mx = m_rel * x
-    if n_max is None:
-        n_max = int(np.ceil(x + 4.0 * x ** (1.0 / 3.0) + 2.0)) + 2
-    ext = 0.0
-    sca = 0.0
+    an = np.empty(n_max, dtype=np.complex128)
+    bn = np.empty(n_max, dtype=np.complex128)
     for n in range(1, n_max + 1):
         ps_x, dps_x = _psi(n, x), _dpsi(n, x)
         ps_m, dps_m = _psi(n, mx), _dpsi(n, mx)
         xi_x, dxi_x = _xi(n, x), _dxi(n, x)
-        an = (m_rel * ps_m * dps_x - ps_x * dps_m) / (m_rel * ps_m * dxi_x - xi_x * dps_m)
-        bn = (ps_m * dps_x - m_rel * ps_x * dps_m) / (ps_m * dxi_x - m_rel * xi_x * dps_m)
-        ext += (2 * n + 1) * np.real(an + bn)
-        sca += (2 * n + 1) * (abs(an) ** 2 + abs(bn) ** 2)
+        an[n - 1] = (m_rel * ps_m * dps_x - ps_x * dps_m) / (m_rel * ps_m * dxi_x - xi_x * dps_m)
+        bn[n - 1] = (ps_m * dps_x - m_rel * ps_x * dps_m) / (ps_m * dxi_x - m_rel * xi_x * dps_m)
+    return an, bn
+
+
+def mie_cross_sections(m_rel: complex, k: float, a: float, n_max=None):
+    x = k * a
+    if n_max is None:
+        n_max = int(np.ceil(x + 4.0 * x ** (1.0 / 3.0) + 2.0)) + 2
+    an, bn = mie_coefficients(m_rel, x, n_max)
+    n = np.arange(1, n_max + 1)
     f = 2.0 * np.pi / k ** 2
-    return f * ext, f * sca
+    return f * float(np.sum((2 * n + 1) * np.real(an + bn))), f * float(np.sum((2 * n + 1) * (abs(an) ** 2 + abs(bn) ** 2)))

@@ -407,6 +407,120 @@ def test_dda_plane_wave_converges_to_mie():
     assert errs[0] > errs[-1]
 
 
+def test_mie_projection_reproduces_plane_wave_cross_sections():
+    """The regular-wave projection, Mie scattering and flux sums of
+    oracle/mie_eels.py, fed a plane wave, give the textbook C_ext and C_sca."""
+    from oracle import mie_eels
+    from oracle.constants import C_LIGHT
+    for m_rel, x, m_h in ((1.5 + 0.1j, 0.8, 1.0), (0.3 + 3.0j, 1.7, 1.45), (1.33 + 0j, 3.0, 1.2)):
+        k = 1.0e7
+        a = x / k
+        Z = MU0 * C_LIGHT / m_h
+
+        def e_fn(r):
+            out = np.zeros((len(r), 3), dtype=complex)
+            out[:, 0] = np.exp(1j * k * r[:, 2])
+            return out
+
+        def h_fn(r):
+            out = np.zeros((len(r), 3), dtype=complex)
+            out[:, 1] = np.exp(1j * k * r[:, 2]) / Z
+            return out
+
+        cM, cN = mie_eels.regular_coefficients(e_fn, h_fn, k, Z, 1.3 * a, 20)
+        w_ext, w_sca = mie_eels.powers(cM, cN, m_rel, k, a, Z)
+        ext, sca = mie_cross_sections(m_rel, k, a, n_max=20)
+        assert w_ext * 2 * Z == pytest.approx(ext, rel=1e-12)        # I0 = 1 / (2 Z)
+        assert w_sca * 2 * Z == pytest.approx(sca, rel=1e-12)
+
+
+def test_electron_magnetic_field_is_the_curl_of_eq25():
+    """H = curl(I1 e_z) (Eq. 22-23) against curl(E_inc) / (i w mu0) of
+    Eq. 25 by central differences."""
+    from oracle import mie_eels
+    v = physics.electron_speed(120.0)
+    for eps_h in (1.0, 2.1025, 4.0 + 0.3j):
+        m_h = physics.host_index(eps_h)
+        _, gam = physics.beta_gamma_h(v, m_h)
+        w = physics.omega_of(2.2)
+        r0 = np.array([[3e-9, -4e-9, 2e-9], [-6e-9, 1e-9, -5e-9]])
+        x0, y0 = 14e-9, 2e-9
+        h = 1e-12
+        curl = np.zeros((2, 3), dtype=complex)
+        grads = []
+        for ax in range(3):
+            dr = np.zeros(3)
+            dr[ax] = h
+            ep = field.incident_field(r0 + dr, w, v, m_h, gam, x0, y0)
+            em = field.incident_field(r0 - dr, w, v, m_h, gam, x0, y0)
+            grads.append((ep - em) / (2 * h))          # d E / d x_ax
+        curl[:, 0] = grads[1][:, 2] - grads[2][:, 1]
+        curl[:, 1] = grads[2][:, 0] - grads[0][:, 2]
+        curl[:, 2] = grads[0][:, 1] - grads[1][:, 0]
+        ref = curl / (1j * w * MU0)
+        got = mie_eels.electron_H(r0, w, v, gam, x0, y0)
+        assert np.linalg.norm(got - ref) <= 1e-6 * np.linalg.norm(got)
+
+
+def test_mie_eels_small_sphere_and_lossless_limits():
+    """Mie EELS/CL of a small sphere tends to the dipole formulas (the N = 1
+    case of Eq. 37 and Eq. 42) with an error shrinking like a^2; a lossless
+    sphere scatters all it extinguishes (W_ext = W_sca for any incident
+    field)."""
+    from oracle import mie_eels
+    v = physics.electron_speed(100.0)
+    e = 2.0
+    for eps_h in (1.0, 2.1025):
+        eps_p = I.drude(e)
+        m_h = np.sqrt(eps_h)
+        w = physics.omega_of(e)
+        k = m_h * w / C_LIGHT
+        _, gam = physics.beta_gamma_h(v, m_h)
+        b = 10e-9
+        e0 = field.incident_field(np.zeros((1, 3)), w, v, m_h, gam, b, 0.0)[0]
+        errs = []
+        for a in (1e-9, 0.5e-9):
+            pe, pc = mie_eels.eels_cl_sphere(a, eps_p, eps_h, e, b, v, n_max=12)
+            m2 = eps_p / eps_h
+            acm = a ** 3 * (m2 - 1) / (m2 + 2)
+            al = acm / (1 - 2j / 3 * k ** 3 * acm)
+            pe_d = 4 * EPS0 * eps_h / HBAR ** 2 * np.imag(al) * np.sum(abs(e0) ** 2) * E_CHARGE
+            pc_d = 8 / 3 * EPS0 * eps_h * k ** 3 * np.sum(abs(al * e0) ** 2) / HBAR ** 2 * E_CHARGE
+            errs.append((abs(pe / pe_d - 1), abs(pc / pc_d - 1)))
+        assert errs[1][0] < 1e-3 and errs[1][1] < 1e-3
+        assert 3.0 < errs[0][0] / errs[1][0] < 5.0                 # O(a^2)
+        coef = mie_eels.electron_coefficients(eps_h, 2.4, 25e-9, v, 16, 17e-9)
+        pe, pc = mie_eels.eels_cl_from(coef, 12e-9, 2.5 * eps_h, eps_h)
+        assert pe == pytest.approx(pc, rel=1e-10)
+
+
+def test_dda_eels_and_cl_converge_to_mie():
+    """The oracle's DDA P_EELS and P_CL of a sphere (volume-equivalent radius)
+    approach the Lorenz-Mie solution as the lattice is refined, in vacuum
+    and in glass (Sec. 3.2 compares with Mie the same way).  Absorbing
+    dielectric spheres: the CM polarizability converges slowly for metals
+    (|m| ~ 4, Re eps < 0), whose errors at these sizes are of order one both
+    for electron and for plane-wave excitation."""
+    from oracle import mie_eels
+    ek = 100.0
+    v = physics.electron_speed(ek)
+    diam, b, e = 20.0, 25.0, 2.5
+    for eps_h, eps_p in ((1.0, 2.25 + 0.5j), (2.1025, 4.0 + 1.0j)):
+        coef = mie_eels.electron_coefficients(eps_h, e, b * NM, v, 16, 17.5 * NM)
+        errs = []
+        for n in (8, 12, 16, 20):
+            occ = I.sphere_occupancy(n, diam)
+            d = diam / n
+            a_eq = (3 * int(occ.sum()) / (4 * np.pi)) ** (1 / 3) * d
+            pe, pc = mie_eels.eels_cl_from(coef, a_eq * NM, eps_p, eps_h)
+            o = run.solve_point(n, n, n, d, occ, e, [eps_p], eps_h, (b, 0.0), ekin_keV=ek, method="fft",
+                                rtol=1e-10)
+            errs.append((abs(o["P_EELS"] / pe - 1), abs(o["P_CL"] / pc - 1)))
+        for j in (0, 1):
+            assert all(errs[i + 1][j] < errs[i][j] for i in range(3)), (eps_h, errs)
+        assert errs[-1][0] < 0.01 and errs[-1][1] < 0.01, (eps_h, errs)
+
+
 def test_small_sphere_eels_dipole_limit():
     """A sphere much smaller than b: the DDA loss tends to the single-dipole
     loss of the whole sphere, alpha~ = a^3 (m^2-1)/(m^2+2) (radiative
