@@ -344,8 +344,9 @@ __global__ void k_qmr2_start(KrylovArgs<Rl> k) {
     q.inv_rho = 0.0;
     if (rho > 0.0) {
         q.inv_rho = 1.0 / rho;
+        // v_1^T v_1 ~ 0 is left to the first step's breakdown checks, after
+        // k_qmr2_scale has zeroed x (a system stopped here would keep a stale x)
         q.delta = make_double2(o[0] / (rho * rho), o[1] / (rho * rho));
-        if (!(cabs_(q.delta) >= 1e-30)) q.status = 3;   // v_1^T v_1 = 0: no Lanczos step
     } else {                        // zero right-hand side: x = 0 is exact
         q.status = 1;
         q.qres = 0.0;
