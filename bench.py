@@ -1,14 +1,17 @@
 """Benchmark: EELS/CL (energy, beam) points per second on one GB300.
 
-Default workload: the 30 nm Drude-gold sphere on a 32^3 lattice (17,256
-dipoles, 64^3 padded FFT) in an n = 1.45 host, 120 keV electron at b = 20 nm,
-200 loss energies 1.0-4.0 eV -- one EELS + CL spectrum per step, solved in
-the mixed path (FP32 QMR to 1e-5 inside FP64 refinement to 1e-8; FP64
-incident field and loss sums; CL far field on 2562 directions).
+Default workload: the 100 nm Drude-silver sphere on a 64^3 lattice (137,376
+dipoles, 128^3 padded FFT) in the absorbing Cherenkov host eps_h = 4 + 0.05i,
+200 keV electron (beta_h > 1) at b = 60 nm, 100 loss energies 1.5-4.0 eV,
+CL far field on 2562 directions -- the largest single-GPU workload.  The
+mixed path: FP32 QMR inside FP64 refinement to 1e-8, FP64 incident field
+and loss sums.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload ...]
 
-A step is one eels_solve over every point of the workload.  `value` is
+A step is one eels_solve over one batch of the workload: 25 energies of the
+Cherenkov spectrum (the steps cycle through its four batches, so K = 20
+covers it five times), all 200 energies of the 32^3 spectrum.  `value` is
 device-timed (CUDA events on the library's stream, the lattice already set);
 `e2e` adds the host->device copy of the inputs (eels_set_grid + host input
 arrays) and the device->host copy of the outputs through the same C ABI.
@@ -37,26 +40,36 @@ from paper_2208_01348_gb300 import inputs as I  # noqa: E402
 METRIC = "EELS points/s at rel.err≤1e-4 vs FP64 oracle; matvec HBM-roofline %; p50/p99 ms"
 
 WORKLOADS = {
+    "cherenkov": lambda: I.config_cherenkov(),
     "spectrum": lambda: I.config_spectrum(),
     "small": lambda: I.config_small_sphere(),
-    "cherenkov": lambda: I.config_cherenkov(),
     "rod": lambda: I.config_rod_map(n_energy=8, nbx=32, nby=32),
 }
-# a bounded oracle sample per workload: (energy index, beam index)
-CPU_SAMPLE = {"spectrum": (100, 0), "small": (0, 0), "cherenkov": (50, 0), "rod": (4, 0)}
+# energies per step (one batch of the workload; the steps cycle through the spectrum)
+STEP_ENERGIES = {"cherenkov": 25, "spectrum": 200, "small": 1, "rod": 1}
+
+# The oracle sample of the CPU baseline, per workload: the point (energy
+# index, beam index); None, or the GMRES iterations timed and the direction
+# stride of the far field timed (the oracle at full size takes tens of
+# minutes per point on a host: its point time is modelled from the timed
+# parts, see oracle_point()), with the GMRES matvecs the oracle needs for
+# that point (bench.py --oracle-iterations prints them).
+CPU_SAMPLE = {"spectrum": (100, 0, None), "small": (0, 0, None),
+              "cherenkov": (50, 0, dict(iters=6, cl_stride=32, matvecs=1937)),
+              "rod": (4, 0, dict(iters=6, cl_stride=8, matvecs=None))}
 
 # ncu DRAM traffic (read + write bytes) of one matvec launch set, per system,
-# measured on the 64^3-FFT kernels of the spectrum workload whose sources hash
-# to TRAFFIC_SRC_HASH; reported as null for other workloads (other FFT sizes,
+# measured on the workload TRAFFIC_WORKLOAD with kernel sources that hash to
+# TRAFFIC_SRC_HASH; reported as null for other workloads (other FFT sizes,
 # other kernels) and when the kernel sources differ from the measured ones.
-TRAFFIC_BYTES_PER_SYSTEM = 13_713_772       # profiles/fft_matvec_sphere32_64systems.md
-TRAFFIC_SRC_HASH = "730a9a2c5c0e6dec"
-TRAFFIC_WORKLOAD = "spectrum"
+TRAFFIC_BYTES_PER_SYSTEM = None
+TRAFFIC_SRC_HASH = ""
+TRAFFIC_WORKLOAD = "cherenkov"
 
 
 def kernel_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_fft.cu", "fft.cuh", "kernels.h", "common.cuh"):
+    for f in ("k_fft.cu", "k_xreg.cu", "fft.cuh", "fft_warp.cuh", "kernels.h", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2208_01348_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -128,53 +141,128 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(wname: str, w):
-    """The oracle (FP64, scipy FFT convolution + GMRES to 1e-8) on one point."""
-    from oracle import run
-    ie, ib = CPU_SAMPLE[wname]
-    t0 = time.perf_counter()
+def oracle_point(wname: str, w):
+    """One point of the workload through the FP64 oracle on the host cores.
+    Small workloads: the full solve (scipy FFT convolution + GMRES(200) to
+    1e-8) and every loss.  Full-size Cherenkov sphere and rod map: the same
+    setup (fields, D-hat), the first `iters` GMRES(200) iterations, the
+    P_EELS / P_ext / P_abs sums and the far field on every cl_stride-th
+    direction are timed, and the point time is modelled as setup +
+    matvecs x (time per timed iteration) + losses + cl_stride x far field.
+    The first iterations of a restart cycle orthogonalise against fewer
+    vectors than the average one, so the modelled time is a lower bound
+    and the CPU figure an upper bound."""
+    import scipy.sparse.linalg as spla
+    from oracle import green, losses, run
+    ie, ib, smp = CPU_SAMPLE[wname]
     g = w.grid
+    point = f"{w.name} energy {w.energies_eV[ie]:.3f} eV (index {ie}), beam {ib}"
+    t0 = time.perf_counter()
     pt = run.setup(g.nx, g.ny, g.nz, g.d_nm, g.occ, w.energies_eV[ie], w.eps_p[ie], w.eps_h[ie], w.beams_nm[ib],
                    ekin_keV=w.ekin_keV)
-    p, _ = run.solve_fft(pt, rtol=1e-8)
-    run.observables(pt, p)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"1 point of {w.name}: energy {w.energies_eV[ie]:.3f} eV (index {ie}), beam {ib}; "
-                      f"oracle per-point time varies strongly with energy (GMRES iterations)",
-            "seconds": dt}
+    if smp is None:
+        p, _ = run.solve_fft(pt, rtol=1e-8)
+        run.observables(pt, p)
+        dt = time.perf_counter() - t0
+        return {"seconds": dt, "cpu_seconds": dt, "sample": f"1 point of {point}, solved in full"}
+    op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha)
+    t_setup = time.perf_counter() - t0
+    sq = np.sqrt(pt.alpha)
+    n3 = 3 * len(pt.r)
+    count = [0]
+
+    class _Enough(Exception):
+        pass
+
+    def mv(y):
+        if count[0] >= smp["iters"] + 1:          # the initial residual and `iters` iterations
+            raise _Enough
+        count[0] += 1
+        y = y.reshape(-1, 3)
+        return (sq[:, None] * op.matvec(sq[:, None] * y)).reshape(-1)
+
+    L = spla.LinearOperator((n3, n3), matvec=mv, dtype=np.complex128)
+    b = (sq[:, None] * pt.E_inc).reshape(-1)
+    t1 = time.perf_counter()
+    try:
+        spla.gmres(L, b, rtol=1e-8, atol=0.0, restart=200, maxiter=20000)
+    except _Enough:
+        pass
+    t_iter = (time.perf_counter() - t1) / count[0]
+    p = np.zeros_like(pt.E_inc)                   # the timed sums do not depend on the values
+    t2 = time.perf_counter()
+    losses.p_eels(pt.E_a, p, pt.eps_h, pt.omega)
+    losses.p_ext(pt.E_inc, p, pt.eps_h, pt.omega)
+    losses.p_abs(p, pt.alpha_cm, pt.eps_h, pt.omega)
+    t3 = time.perf_counter()
+    dirs, wts = run.directions()
+    st = smp["cl_stride"]
+    losses.p_cl(pt.r, p, pt.k, pt.m_h, pt.omega, dirs[::st], wts[::st])
+    t4 = time.perf_counter()
+    n_mv = smp["matvecs"] or 1000
+    seconds = t_setup + n_mv * t_iter + (t3 - t2) + st * (t4 - t3)
+    return {"seconds": seconds, "cpu_seconds": t4 - t0,
+            "sample": (f"1 point of {point}: setup, {count[0]} of the {n_mv} GMRES(200) matvecs it needs"
+                       + ("" if smp["matvecs"] else " (assumed)")
+                       + f", the loss sums and 1/{st} of the far-field directions timed; point time modelled as "
+                         f"setup + {n_mv} x time per timed iteration + losses + {st} x far field (a lower bound: "
+                         f"early iterations of a restart cycle are the cheapest)")}
+
+
+def cpu_baseline(wname: str, w):
+    """The oracle (FP64) on a bounded sample of the workload (oracle_point)."""
+    r = oracle_point(wname, w)
+    return {"value": 1.0 / r["seconds"], "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": r["sample"], "seconds_per_point": r["seconds"], "cpu_seconds": r["cpu_seconds"]}
 
 
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import run
-    ie, ib = CPU_SAMPLE[args.workload]
-    g = w.grid
-
-    def step():
-        pt = run.setup(g.nx, g.ny, g.nz, g.d_nm, g.occ, w.energies_eV[ie], w.eps_p[ie], w.eps_h[ie], w.beams_nm[ib],
-                       ekin_keV=w.ekin_keV)
-        p, _ = run.solve_fft(pt, rtol=1e-8)
-        run.observables(pt, p)
-
     for _ in range(args.warmup):
-        step()
+        oracle_point(args.workload, w)
     t0 = time.perf_counter()
+    secs = []
     for _ in range(args.steps):
-        step()
-    dt = (time.perf_counter() - t0) / args.steps
-    v = 1.0 / dt
-    sample = f"1 point per step of {w.name}: energy {w.energies_eV[ie]:.3f} eV (index {ie}), beam {ib}"
+        r = oracle_point(args.workload, w)
+        secs.append(r["seconds"])
+    wall = (time.perf_counter() - t0) / args.steps
+    v = 1.0 / float(np.mean(secs))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "oracle": "FP64 numpy/scipy: FFT convolution + GMRES to 1e-8"},
-        "cpu_baseline": {"value": v, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+        "config": {"workload": w.name, "oracle": "FP64 numpy/scipy: FFT convolution + GMRES(200) to 1e-8"},
+        "cpu_baseline": {"value": v, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "per step: " + r["sample"]},
         "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def run_oracle_iterations(args, w):
+    """Runs the oracle's GMRES(200) on the CPU-baseline point of the workload
+    to 1e-8 and prints how many matvecs it needed (the constant of CPU_SAMPLE)."""
+    import scipy.sparse.linalg as spla
+    from oracle import green, run
+    ie, ib, _ = CPU_SAMPLE[args.workload]
+    g = w.grid
+    pt = run.setup(g.nx, g.ny, g.nz, g.d_nm, g.occ, w.energies_eV[ie], w.eps_p[ie], w.eps_h[ie], w.beams_nm[ib],
+                   ekin_keV=w.ekin_keV)
+    op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha)
+    sq = np.sqrt(pt.alpha)
+    count = [0]
+
+    def mv(y):
+        count[0] += 1
+        y = y.reshape(-1, 3)
+        return (sq[:, None] * op.matvec(sq[:, None] * y)).reshape(-1)
+
+    n3 = 3 * len(pt.r)
+    L = spla.LinearOperator((n3, n3), matvec=mv, dtype=np.complex128)
+    _, info = spla.gmres(L, (sq[:, None] * pt.E_inc).reshape(-1), rtol=1e-8, atol=0.0, restart=200, maxiter=20000)
+    print(json.dumps({"workload": w.name, "energy_index": ie, "beam_index": ib, "info": int(info),
+                      "matvecs": count[0]}))
 
 
 def run_matvec_only(args):
@@ -296,7 +384,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="spectrum", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--workload", default="cherenkov", choices=sorted(WORKLOADS) + ["serve"])
+    ap.add_argument("--step-energies", type=int, default=0,
+                    help="energies per step (0: the workload's default batch)")
+    ap.add_argument("--oracle-iterations", action="store_true",
+                    help="run the oracle to convergence on the CPU-baseline point and print its matvec count")
     ap.add_argument("--matvec-only", type=int, default=0,
                     help="time only the FFT matvec on this many systems of the workload (profiling)")
     ap.add_argument("--serve-requests", type=int, default=16)
@@ -316,6 +408,9 @@ def main():
         run_matvec_only(args)
         return
     w = WORKLOADS[args.workload]()
+    if args.oracle_iterations:
+        run_oracle_iterations(args, w)
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -352,52 +447,70 @@ def main():
                                 solver={"qmr2": dd.EELS_QMR2, "qmr": dd.EELS_QMR, "bicgstab": dd.EELS_BICGSTAB}[args.solver])
     dd.eels_set_grid(ctx, g.occ, g.d_nm)
 
-    def step():
-        return dd.eels_solve(ctx, opts, w.energies_eV, w.eps_p, w.eps_h, w.beams_nm, want_cl=True)
+    # one step = one batch of the workload: E consecutive energies (all beams);
+    # step k takes batch k mod n_batches
+    n_e = len(w.energies_eV)
+    E = min(args.step_energies or STEP_ENERGIES.get(args.workload, n_e), n_e)
+    batches = [np.arange(i, min(i + E, n_e)) for i in range(0, n_e, E)]
+    n_beam = len(w.beams_nm)
 
-    for _ in range(args.warmup):
-        res = step()
-    assert res.converged.all(), "warm-up solve did not converge"
+    def step(k):
+        ie = batches[k % len(batches)]
+        return ie, dd.eels_solve(ctx, opts, w.energies_eV[ie], w.eps_p[ie], w.eps_h[ie], w.beams_nm, want_cl=True)
+
+    for k in range(args.warmup):
+        _, res = step(k)
+        assert res.converged.all(), "warm-up solve did not converge"
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = dd.eels_kernel_launches()
+    pts_timed = 0
+    results = {}
     with ClockSampler(local) as clk:
         ev0.record(stream)
-        for _ in range(args.steps):
-            res = step()
+        for k in range(args.steps):
+            ie, res = step(k)
+            pts_timed += len(ie) * n_beam
+            results[k % len(batches)] = (ie, res)
         ev1.record(stream)
         torch.cuda.synchronize()
     launches = dd.eels_kernel_launches() - l0
     barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_total = ev0.elapsed_time(ev1)
     if dist:
-        t = torch.tensor([ms], device="cuda")
+        t = torch.tensor([ms_total], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    pts = w.n_points * world
-    value = pts / (ms * 1e-3)
+        ms_total = float(t.item())
+    ms = ms_total / args.steps
+    value = pts_timed * world / (ms_total * 1e-3)
     clocks = clk.summary()
+    iters = np.concatenate([r.iters.ravel() for _, r in results.values()])
+    resid = np.concatenate([r.residual.ravel() for _, r in results.values()])
 
     # end to end through the host API: lattice upload + host inputs + host outputs
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    pts_e2e, h2d, d2h = 0, 0, 0
+    for k in range(args.e2e_steps):
         dd.eels_set_grid(ctx, g.occ, g.d_nm)
-        r2 = step()
+        ie, r2 = step(k)
+        pts_e2e += len(ie) * n_beam
+        h2d += g.occ.nbytes + 8 * len(ie) + 16 * w.eps_p[ie].size + 16 * len(ie) + w.beams_nm.nbytes
+        d2h += len(ie) * n_beam * (4 * 8 + 24)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.e2e_steps
+    e2e_s = time.perf_counter() - t0
     if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
+        t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    h2d = g.occ.nbytes + w.energies_eV.nbytes + w.eps_p.nbytes + w.eps_h.nbytes + w.beams_nm.nbytes
-    d2h = 4 * w.n_points * 8 + w.n_points * 24
+        e2e_s = float(t.item())
 
-    # roofline of the FFT matvec (the dominant kernel set) on this workload's systems
-    S = len(w.energies_eV)
+    # roofline of the FFT matvec (the dominant kernel set) on one batch's systems
+    S = len(batches[0]) * n_beam
     tiles = dd.eels_tile_widths(ctx)
-    dd.eels_prepare_operator(ctx, w.energies_eV, w.eps_p, w.eps_h)
+    ie0 = batches[0]
+    dd.eels_prepare_operator(ctx, np.repeat(w.energies_eV[ie0], n_beam), np.repeat(w.eps_p[ie0], n_beam, axis=0),
+                             np.repeat(w.eps_h[ie0], n_beam))
     n = dd.eels_num_dipoles(ctx)
     mx, my, mz = dd.eels_padded_dims(ctx)
     x = torch.randn(S, 3, n, dtype=torch.complex64, device="cuda")
@@ -414,7 +527,7 @@ def main():
     mv_ms = m0.elapsed_time(m1) / args.matvec_reps
     M = mx * my * mz
     Mr = (mx // 2 + 1) * (my // 2 + 1) * (mz // 2 + 1)
-    alg_bytes = S * (6 * M + 6 * Mr + 6 * n) * 8      # complex64, one beam per energy (B = 1)
+    alg_bytes = S * (6 * M + 6 * Mr + 6 * n) * 8      # complex64, one system per D-hat read (B = 1)
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (mv_ms * 1e-3) / 1e9
     traffic = None
@@ -425,8 +538,12 @@ def main():
     # the plain FP64 path, one system per solve, on a sample of the energies
     # (first beam): its points/s, and how far the mixed results are from it
     fp64_cmp = None
-    if prec == dd.EELS_MIXED and world == 1 and args.fp64_sample > 0:
-        idx = np.unique(np.linspace(0, len(w.energies_eV) - 1, args.fp64_sample).round().astype(int))
+    if prec == dd.EELS_MIXED and world == 1 and args.fp64_sample > 0 and results:
+        ie_all = np.concatenate([v[0] for v in results.values()])
+        pe_all = np.concatenate([v[1].p_eels[:, 0] for v in results.values()])
+        pc_all = np.concatenate([v[1].p_cl[:, 0] for v in results.values()])
+        pick = np.unique(np.linspace(0, len(ie_all) - 1, args.fp64_sample).round().astype(int))
+        idx = ie_all[pick]
         o64 = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=dd.EELS_FP64, eps_it=1e-8, n_dir=w.n_dir,
                                    max_batch=1)
         dd.eels_set_grid(ctx, g.occ, g.d_nm)
@@ -435,11 +552,11 @@ def main():
         r64 = dd.eels_solve(ctx, o64, w.energies_eV[idx], w.eps_p[idx], w.eps_h[idx], w.beams_nm[:1], want_cl=True)
         torch.cuda.synchronize()
         v64 = len(idx) / (time.perf_counter() - t0)
-        rel_e = np.abs(res.p_eels[idx, 0] - r64.p_eels[:, 0]) / np.abs(r64.p_eels[:, 0])
-        rel_c = np.abs(res.p_cl[idx, 0] - r64.p_cl[:, 0]) / np.abs(r64.p_cl[:, 0])
+        rel_e = np.abs(pe_all[pick] - r64.p_eels[:, 0]) / np.abs(r64.p_eels[:, 0])
+        rel_c = np.abs(pc_all[pick] - r64.p_cl[:, 0]) / np.abs(r64.p_cl[:, 0])
         fp64_cmp = {"value": v64, "unit": "points/s",
                     "sample": f"energies {idx.tolist()} of {w.name}, beam 0, one system per solve, eps 1e-8",
-                    "mixed_over_fp64": value / v64, "p_eels_max_rel_diff": float(rel_e.max()),
+                    "mixed_over_fp64": value / world / v64, "p_eels_max_rel_diff": float(rel_e.max()),
                     "p_cl_max_rel_diff": float(rel_c.max())}
     dd.eels_destroy(ctx)
 
@@ -450,14 +567,16 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if prec == dd.EELS_MIXED else "f64",
         "data": "synthetic (Drude permittivities stand in for tabulated optical data)",
-        "config": {"workload": w.name, "points_per_gpu": w.n_points, "dipoles": n, "fft": [mx, my, mz],
-                   "precision": args.precision, "solver": args.solver, "x_tile": list(tiles), "eps_it": 1e-8, "eps_inner": 1e-5, "n_dir": w.n_dir,
-                   "l2": "working set of a step > L2 (several GB of per-system vectors)",
-                   "iters_mean": float(np.mean(res.iters)), "residual_max": float(np.max(res.residual))},
-        "e2e": {"value": pts / (e2e_ms * 1e-3), "unit": "points/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms},
-        "roofline": {"bound": "hbm", "kernel": (f"fft_matvec (3 launches: slab forward, x pass, slab inverse; {mx}x{my}x{mz} FFT"
-                               + (", k_slab_fwd64 / k_xpassc<float,16,64> / k_slab_inv64)" if (mx, my, mz) == (64, 64, 64) else ")")),
+        "config": {"workload": w.name, "points_per_gpu": n_e * n_beam, "points_per_step": E * n_beam,
+                   "step": f"{E} energies x {n_beam} beams, batches cycled", "dipoles": n, "fft": [mx, my, mz],
+                   "precision": args.precision, "solver": args.solver, "x_tile": list(tiles), "eps_it": 1e-8,
+                   "eps_inner": 1e-5, "n_dir": w.n_dir,
+                   "l2": "working set of a step > L2 (several GB of per-system vectors and FFT scratch)",
+                   "iters_mean": float(np.mean(iters)), "residual_max": float(np.max(resid))},
+        "e2e": {"value": pts_e2e * world / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d / args.e2e_steps),
+                "d2h_bytes_per_step": int(d2h / args.e2e_steps), "ms_per_step": e2e_s * 1e3 / args.e2e_steps},
+        "roofline": {"bound": "hbm",
+                     "kernel": f"fft_matvec (3 launches: slab forward, x pass, slab inverse; {mx}x{my}x{mz} FFT)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic, "ms_per_matvec": mv_ms, "systems": S,
                      "alg_bytes": alg_bytes},

@@ -31,7 +31,8 @@
  * EELS_E_NOT_CONVERGED, see below).  A context owns all device memory it
  * allocates and frees it in eels_destroy.  Device-pointer entry points
  * (suffix _dev) read and write caller device memory on the given stream and
- * return once the work is enqueued (the caller synchronises).
+ * return once the work is enqueued (the caller synchronises), unless their
+ * comment says otherwise.
  *
  * Errors: every int-returning call returns 0 on success or a negative
  * EELS_E_* code; eels_last_error(ctx) describes the last failure of that
@@ -157,6 +158,28 @@ int eels_solve(eels_ctx* ctx, const eels_opts* opts, int n_energy, const double*
                eels_c128* p_out, eels_point_stats* stats);
 
 /*
+ * eels_solve with every array argument in DEVICE memory of the context's
+ * device (the problem statement of Sec. 2, as for eels_solve): energy_eV
+ * [n_energy] double, eps_p [n_energy][n_mat] and eps_h [n_energy]
+ * eels_c128, beams [n_beam] eels_beam; outputs p_eels (required), p_cl,
+ * p_ext, p_abs [n_energy][n_beam] double, p_out [n_energy][n_beam][N][3]
+ * eels_c128, stats [n_energy][n_beam] eels_point_stats (any output but p_eels
+ * may be NULL).  opts is a host struct.  The inputs are read, and the
+ * outputs written, in the order of cuda_stream (a cudaStream_t; NULL = the
+ * legacy default stream, e.g. torch.cuda.current_stream()); the solve itself
+ * runs on the context's stream.  The call returns once the outputs are in
+ * place (it synchronises cuda_stream).  The caller's current device must be
+ * the context's.  Results are bit-identical to eels_solve on the same inputs.
+ * Errors as eels_solve, plus EELS_E_INVALID_ARG for a host or foreign-device
+ * pointer (checked with cudaPointerGetAttributes before any work).
+ */
+int eels_solve_dev(eels_ctx* ctx, const eels_opts* opts, int n_energy, const double* energy_eV,
+                   int n_mat, const eels_c128* eps_p, const eels_c128* eps_h,
+                   int n_beam, const eels_beam* beams,
+                   double* p_eels, double* p_cl, double* p_ext, double* p_abs,
+                   eels_c128* p_out, eels_point_stats* stats, void* cuda_stream);
+
+/*
  * Asynchronous form of eels_solve.  The inputs are copied before return; the
  * solve runs on a host thread of the library, on the context's stream.  The
  * outputs are written into the caller's buffers (same meaning and layout as
@@ -217,12 +240,38 @@ int eels_prepare_operator(eels_ctx* ctx, int n_energy, const double* energy_eV, 
 
 /* y = A' x for n_sys prepared systems (n_sys <= n_energy of the last
  * eels_prepare_operator).  x, y: DEVICE arrays [n_sys][3][N] (component-major
- * per system) of complex64 (precision EELS_MIXED) or complex128
+ * per system; dipoles in the library's internal order: the occupied cells
+ * sorted by ix, then iy, then iz, iz fastest) of complex64 (precision EELS_MIXED) or complex128
  * (EELS_FP64); x and y must not overlap.  Enqueued on cuda_stream (NULL =
  * legacy default stream); the context's FFT scratch is used, so calls on one
- * context must not overlap in time.  This is the FFT matrix-vector product
- * every Krylov iteration applies. */
+ * context must not overlap in time.  The caller's current device must be the
+ * context's (EELS_E_INVALID_ARG otherwise).  This is the FFT matrix-vector
+ * product every Krylov iteration applies. */
 int eels_matvec_dev(eels_ctx* ctx, int precision, const void* x, void* y, int n_sys, void* cuda_stream);
+
+/* One Krylov solve A' x = b on the operator prepared by
+ * eels_prepare_operator (the Jacobi-scaled form of the dipole system of
+ * Eq. 8, solved in the paper's code by QMR or BiCGStab, Sec. S5), for n_sys
+ * systems (n_sys <= n_energy of the last eels_prepare_operator):
+ *   b, x: DEVICE arrays [n_sys][3][N] (component-major per system, dipoles in
+ *   the internal order of eels_matvec_dev) of complex64
+ *   (precision EELS_MIXED: FP32 vectors and matvecs, FP64 scalars) or
+ *   complex128 (EELS_FP64); b and x must not overlap.
+ *   solver: EELS_QMR2, EELS_QMR or EELS_BICGSTAB; x starts from 0 and the
+ *   solve stops when the (quasi-)residual norm is <= eps ||b|| or after
+ *   max_iter iterations.
+ *   status, iters: optional HOST arrays [n_sys]: 1 converged, 2 iteration
+ *   limit, 3 breakdown (the Lanczos process of QMR fails when v^T v vanishes,
+ *   e.g. at a right-hand side with b^T b ~ 0: x is then left at 0), and the
+ *   iterations run.
+ * b is read after the work already queued on cuda_stream; x is complete in
+ * the order of cuda_stream when the call returns (the iterations run on the
+ * context's stream, with host reads of the convergence counter between
+ * bursts of graph replays).  The caller's current device must be the
+ * context's.  Uses the context's Krylov buffers: calls on one context must
+ * not overlap in time. */
+int eels_krylov_solve_dev(eels_ctx* ctx, int precision, int solver, const void* b, void* x, int n_sys,
+                          double eps, int max_iter, int* status, int* iters, void* cuda_stream);
 
 /* Kernels launched by this library in this process so far (graph replays
  * count their kernel nodes). */
@@ -241,12 +290,13 @@ long long eels_kernel_launches(void);
  * (EELS_NOALLOC_SCRATCH_BYTES = 64 MiB of device memory, held by every GPU
  * that loads the library until the process exits) and calls no allocator.
  *
- *  - Arguments as for eels_matvec_dev.  The scratch needed is
+ *  - Arguments as for eels_matvec_dev (the current device must be the
+ *    context's).  The scratch needed is
  *    n_sys * 3 * My * Nx * Mz * (8 or 16 bytes); larger requests return
  *    EELS_E_UNSUPPORTED ("pass fewer systems per call") before any launch.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress, with the context's device made current for the
+ *    lookup); make that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; nothing in it has to start at zero (each call writes every
  *    scratch element it reads first).  Calls that overlap on the GPU (two

@@ -227,13 +227,13 @@ struct eels_ctx {
     std::vector<uint8_t> mat_h;    // internal dipole -> material (0-based)
     int max_mat = 0;
     LatticeDev L{};
-    DevBuf cellmap, mat, dip_cell, col_range, tw64[3], tw32[3];
+    DevBuf cellmap, mat, dip_cell, col_range, colinfo, tw64[3], tw32[3];
     // workspace
     DevBuf e64, b64, x64, r64, y64, U, u64, u32;
     DevBuf kv[7];                                          // Krylov vectors V0 V1 P0 P1 P2 W X
     DevBuf part_a, part_b, qmr, bicg, active, upd, counters, outer, res, rnorm, eps_sys;
     DevBuf sysf, coef, diag, wabs, wdv, slot, kappa_sys;
-    DevBuf G, Dr64, Dr32, kappa_slot;
+    DevBuf G, Dr64, Dr32, Dx32, kappa_slot;
     DevBuf lpart, lsums, fpart, fsums, dirs, wts;
     int dirs_n = 0;
     int* pinned = nullptr;
@@ -246,9 +246,9 @@ struct eels_ctx {
     int op_systems = 0;
 
     std::vector<DevBuf*> buffers() {
-        std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
+        std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &colinfo, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
                                   &part_a, &part_b, &qmr, &bicg, &active, &upd, &counters, &outer, &res, &rnorm, &eps_sys,
-                                  &sysf, &coef, &diag, &wabs, &wdv, &slot, &kappa_sys, &G, &Dr64, &Dr32, &kappa_slot,
+                                  &sysf, &coef, &diag, &wabs, &wdv, &slot, &kappa_sys, &G, &Dr64, &Dr32, &Dx32, &kappa_slot,
                                   &lpart, &lsums, &fpart, &fsums, &dirs, &wts};
         for (auto& b : kv) v.push_back(&b);
         for (auto& b : tw64) v.push_back(&b);
@@ -329,6 +329,23 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
                 }
             if (first >= 0) cr[(size_t)iy * nx + ix] = make_int2(first, last + 1);
         }
+    // per (ix, iy) column in the internal numbering: index of its first dipole
+    // minus its first iz, the occupied iz range, and whether every column's
+    // occupied cells are contiguous (then dipole = colinfo.x + iz exactly)
+    std::vector<int4> ci((size_t)nx * ny, make_int4(0, 0, 0, 0));
+    bool contig = true;
+    {
+        int next = 0;
+        for (int ix = 0; ix < nx; ++ix)
+            for (int iy = 0; iy < ny; ++iy) {
+                const int2 r = cr[(size_t)iy * nx + ix];
+                int cnt = 0;
+                for (int iz = 0; iz < nz; ++iz) cnt += c->cellmap_h[((size_t)iz * ny + iy) * nx + ix] >= 0;
+                if (cnt != r.y - r.x) contig = false;
+                ci[(size_t)ix * ny + iy] = make_int4(next - r.x, r.x, r.y, 0);
+                next += cnt;
+            }
+    }
     c->nx = nx; c->ny = ny; c->nz = nz;
     c->N = (int)c->dip_cell_h.size();
     c->d_nm = g->d_nm;
@@ -338,6 +355,7 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     h2d(c->mat, c->mat_h, c->stream);
     h2d(c->dip_cell, c->dip_cell_h, c->stream);
     h2d(c->col_range, cr, c->stream);
+    h2d(c->colinfo, ci, c->stream);
     upload_twiddles(c, 0, Mx);
     upload_twiddles(c, 1, My);
     upload_twiddles(c, 2, Mz);
@@ -349,6 +367,9 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     L.mat = c->mat.as<uint8_t>();
     L.dip_cell = c->dip_cell.as<int>();
     L.col_range = c->col_range.as<int2>();
+    L.colinfo = c->colinfo.as<int4>();
+    L.contig = contig ? 1 : 0;
+    L.nmat = maxm;
     L.px = make_plan(Mx); L.py = make_plan(My); L.pz = make_plan(Mz);
     L.tw64x = c->tw64[0].as<double2>(); L.tw64y = c->tw64[1].as<double2>(); L.tw64z = c->tw64[2].as<double2>();
     L.tw32x = c->tw32[0].as<float2>(); L.tw32y = c->tw32[1].as<float2>(); L.tw32z = c->tw32[2].as<float2>();
@@ -515,7 +536,7 @@ size_t per_system_bytes(const LatticeDev& L, bool fp64) {
 }
 
 size_t per_slot_bytes(const LatticeDev& L) {
-    return (size_t)6 * L.Hx * L.Hy * L.Hz * (sizeof(double2) + sizeof(float2));
+    return (size_t)6 * L.Hx * L.Hy * L.Hz * (sizeof(double2) + 2 * sizeof(float2));
 }
 
 // Iterations allowed per inner solve: an FP32 inner solve may be restarted
@@ -563,6 +584,7 @@ MatvecArgs<Rl> mv_args(eels_ctx* c, int S, const cx<Rl>* x, cx<Rl>* y, const cx<
     a.coef = c->coef.as<double2>();
     a.diag = c->diag.as<double2>();
     a.active = active;
+    a.Dx = sizeof(Rl) == 4 ? c->Dx32.as<float2>() : nullptr;
     a.S = S;
     (void)scaled;
     return a;
@@ -781,6 +803,70 @@ void refine_batch(eels_ctx* c, int S, const eels_opts* o, bool fp64, std::vector
     CK(cudaStreamSynchronize(st));
 }
 
+// One inner Krylov solve of A' x = b on the prepared operator, b and x in
+// the caller's device memory (eels_krylov_solve_dev).  The context's stream
+// waits for the caller's stream before reading b, and the caller's stream
+// waits for the copy of x.
+template <typename Rl>
+void krylov_dev(eels_ctx* c, int solver, const void* b, void* x, int S, double eps, int max_iter, int* status,
+                int* iters, cudaStream_t caller) {
+    cudaStream_t st = c->stream;
+    const int n3 = 3 * c->N;
+    const int nblk = (n3 + RED_CHUNK - 1) / RED_CHUNK;
+    const size_t kvec = (size_t)S * n3 * sizeof(cx<Rl>);
+    for (auto& v : c->kv) v.ensure(kvec);
+    c->part_a.ensure((size_t)S * std::max(nblk, 3 * c->L.Nx) * 4 * sizeof(double));
+    c->part_b.ensure((size_t)S * nblk * 4 * sizeof(double));
+    c->qmr.ensure((size_t)S * sizeof(QmrState));
+    c->bicg.ensure((size_t)S * sizeof(BicgState));
+    c->active.ensure(S * sizeof(int)); c->upd.ensure(S * sizeof(int)); c->counters.ensure(64);
+    c->eps_sys.ensure(S * sizeof(double));
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    struct EvGuard { cudaEvent_t e; ~EvGuard() { cudaEventDestroy(e); } } guard{ev};
+    CK(cudaEventRecord(ev, caller));
+    CK(cudaStreamWaitEvent(st, ev, 0));
+    CK(cudaMemcpyAsync(c->kv[1].p, b, kvec, cudaMemcpyDeviceToDevice, st));   // rhs slot of every solver
+    std::vector<int> one(S, 1), cnt(16, 0);
+    cnt[0] = S;                                                             // systems still iterating
+    std::vector<double> ev_eps(S, eps);
+    h2d(c->active, one, st);
+    h2d(c->counters, cnt, st);
+    h2d(c->eps_sys, ev_eps, st);
+    eels_opts o;
+    eels_default_opts(&o);
+    o.solver = solver;
+    o.max_iter = max_iter;
+    o.inner_max_iter = 0;
+    inner_solve<Rl>(c, S, &o, eps);
+    CK(cudaMemcpyAsync(x, c->kv[6].p, kvec, cudaMemcpyDeviceToDevice, st));
+    std::vector<int> stv(S), itv(S);
+    if (solver == EELS_BICGSTAB) {
+        std::vector<BicgState> h(S);
+        CK(cudaMemcpyAsync(h.data(), c->bicg.p, S * sizeof(BicgState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < S; ++i) { stv[i] = h[i].status; itv[i] = h[i].iters; }
+    } else if (solver == EELS_QMR2) {
+        std::vector<Qmr2State> h(S);
+        CK(cudaMemcpyAsync(h.data(), c->qmr.p, S * sizeof(Qmr2State), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < S; ++i) { stv[i] = h[i].status; itv[i] = h[i].iters; }
+    } else {
+        std::vector<QmrState> h(S);
+        CK(cudaMemcpyAsync(h.data(), c->qmr.p, S * sizeof(QmrState), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < S; ++i) { stv[i] = h[i].status; itv[i] = h[i].iters; }
+    }
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(ev, st));
+    CK(cudaStreamWaitEvent(caller, ev, 0));
+    for (int i = 0; i < S; ++i) {
+        // a system still marked running stopped at the host's iteration cap
+        if (status) status[i] = stv[i] == 0 ? 2 : stv[i];
+        if (iters) iters[i] = itv[i];
+    }
+}
+
 int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* energy_eV, int n_mat,
                const eels_c128* eps_p, const eels_c128* eps_h, int n_beam, const eels_beam* beams, double* p_eels,
                double* p_cl, double* p_ext, double* p_abs, eels_c128* p_out, eels_point_stats* stats) {
@@ -855,6 +941,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         c->res.ensure(S * sizeof(double)); c->rnorm.ensure(S * sizeof(double)); c->eps_sys.ensure(S * sizeof(double));
         c->Dr64.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(double2));
         c->Dr32.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(float2));
+        c->Dx32.ensure((size_t)n_slot * 6 * L.Hx * L.Hy * L.Hz * sizeof(float2));
         // D-hat for the batch energies, in chunks that fit ~1/8 of the system budget
         const int gchunk = (int)std::max<size_t>(1, std::min<size_t>(n_slot, (size_t)std::max(1, S) * per_sys / 8 / gslot + 1));
         c->G.ensure(gchunk * gslot);
@@ -865,7 +952,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
             const int nq = std::min(gchunk, n_slot - q0);
             const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
             launch_dhat_build(L, nq, c->kappa_slot.as<double2>() + q0, c->G.as<double2>(), c->Dr64.as<double2>() + q0 * hs,
-                              c->Dr32.as<float2>() + q0 * hs, st);
+                              c->Dr32.as<float2>() + q0 * hs, st, c->Dx32.as<float2>() + q0 * hs);
         }
         CK(cudaGetLastError());
         // per-system parameters
@@ -904,8 +991,12 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
             // first solve on this lattice: time the x-pass tile widths on this
             // batch (the x pass only scrambles the FFT scratch), before any
             // inner-loop graph is captured; FP64 on a few systems only
-            c->L.xw32 = autotune_xpass<float>(L, mv_args<float>(c, S, c->u32.as<float2>(), c->kv[5].as<float2>(),
-                                                                 c->Dr32.as<float2>(), nullptr, true), st);
+            // (the register-resident FP32 x pass has one shape: 16 kz lines per block)
+            c->L.xw32 = xpass_reg_supported(L) ? 16
+                                               : autotune_xpass<float>(L, mv_args<float>(c, S, c->u32.as<float2>(),
+                                                                                          c->kv[5].as<float2>(),
+                                                                                          c->Dr32.as<float2>(), nullptr,
+                                                                                          true), st);
             c->L.xw64 = autotune_xpass<double>(L, mv_args<double>(c, std::min(S, 8), c->x64.as<double2>(),
                                                                    c->y64.as<double2>(), c->Dr64.as<double2>(),
                                                                    nullptr, true), st);
@@ -976,6 +1067,20 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         }
     }
     return all_conv ? EELS_OK : EELS_E_NOT_CONVERGED;
+}
+
+// Entry points that take the caller's device pointers and stream run on the
+// caller's current device: it must be the context's, whose D-hat, lattice
+// tables and scratch the kernels read.
+void require_current_device(const eels_ctx* c) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{EELS_E_CUDA, "cudaGetDevice failed"};
+    }
+    if (cur != c->device)
+        throw Fail{EELS_E_INVALID_ARG, "the current device (" + std::to_string(cur) + ") is not the context's device (" +
+                                           std::to_string(c->device) + "): make it current before the call"};
 }
 
 template <typename F> int guarded(eels_ctx* c, F&& f) {
@@ -1182,10 +1287,12 @@ int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, c
         const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
         c->Dr64.ensure(hs * sizeof(double2));
         c->Dr32.ensure(hs * sizeof(float2));
+        c->Dx32.ensure(hs * sizeof(float2));
         c->G.ensure((size_t)6 * L.Mx * L.My * L.Mz * sizeof(double2));
         std::vector<double2> ks(1, d2(p.kappa));
         h2d(c->kappa_slot, ks, st);
-        launch_dhat_build(L, 1, c->kappa_slot.as<double2>(), c->G.as<double2>(), c->Dr64.as<double2>(), c->Dr32.as<float2>(), st);
+        launch_dhat_build(L, 1, c->kappa_slot.as<double2>(), c->G.as<double2>(), c->Dr64.as<double2>(), c->Dr32.as<float2>(), st,
+                          c->Dx32.as<float2>());
         std::vector<double2> coef((size_t)S * EELS_MAX_MAT, make_double2(1, 0)), diag((size_t)S * EELS_MAX_MAT);
         for (int s = 0; s < S; ++s)
             for (int m = 0; m < EELS_MAX_MAT; ++m) diag[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? d2(p.alpha_inv[m]) : make_double2(0, 0);
@@ -1246,6 +1353,7 @@ int eels_prepare_operator(eels_ctx* c, int n_energy, const double* energy_eV, in
         const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
         c->Dr64.ensure(S * hs * sizeof(double2));
         c->Dr32.ensure(S * hs * sizeof(float2));
+        c->Dx32.ensure(S * hs * sizeof(float2));
         const size_t gslot = (size_t)6 * L.Mx * L.My * L.Mz * sizeof(double2);
         c->G.ensure(gslot);
         std::vector<double2> kap(S), coef((size_t)S * EELS_MAX_MAT), diag((size_t)S * EELS_MAX_MAT, make_double2(1, 0));
@@ -1259,7 +1367,7 @@ int eels_prepare_operator(eels_ctx* c, int n_energy, const double* energy_eV, in
         h2d(c->kappa_slot, kap, st);
         for (int e = 0; e < S; ++e)
             launch_dhat_build(L, 1, c->kappa_slot.as<double2>() + e, c->G.as<double2>(), c->Dr64.as<double2>() + e * hs,
-                              c->Dr32.as<float2>() + e * hs, st);
+                              c->Dr32.as<float2>() + e * hs, st, c->Dx32.as<float2>() + e * hs);
         h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->slot, slot, st);
         c->U.ensure((size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(double2));
         CK(cudaStreamSynchronize(st));
@@ -1275,6 +1383,7 @@ int eels_matvec_dev(eels_ctx* c, int precision, const void* x, void* y, int n_sy
         if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
         if (n_sys <= 0 || n_sys > c->op_systems || !x || !y)
             throw Fail{EELS_E_INVALID_ARG, "matvec_dev: n_sys must be in [1, prepared systems]"};
+        require_current_device(c);
         cudaStream_t st = (cudaStream_t)stream;
         if (precision == EELS_FP64) {
             MatvecArgs<double> a = mv_args<double>(c, n_sys, (const double2*)x, (double2*)y, c->Dr64.as<double2>(), nullptr, true);
@@ -1288,9 +1397,83 @@ int eels_matvec_dev(eels_ctx* c, int precision, const void* x, void* y, int n_sy
     });
 }
 
+int eels_krylov_solve_dev(eels_ctx* c, int precision, int solver, const void* b, void* x, int n_sys, double eps,
+                          int max_iter, int* status, int* iters, void* stream) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
+        if (n_sys <= 0 || n_sys > c->op_systems || !b || !x || b == x)
+            throw Fail{EELS_E_INVALID_ARG, "krylov_solve_dev: n_sys must be in [1, prepared systems], b and x distinct"};
+        if (!(eps > 0) || max_iter <= 0) throw Fail{EELS_E_INVALID_ARG, "krylov_solve_dev: eps and max_iter must be positive"};
+        if (precision != EELS_FP64 && precision != EELS_MIXED) throw Fail{EELS_E_INVALID_ARG, "unknown precision"};
+        if (solver != EELS_QMR && solver != EELS_BICGSTAB && solver != EELS_QMR2)
+            throw Fail{EELS_E_INVALID_ARG, "unknown solver"};
+        require_current_device(c);
+        if (precision == EELS_FP64)
+            krylov_dev<double>(c, solver, b, x, n_sys, eps, max_iter, status, iters, (cudaStream_t)stream);
+        else
+            krylov_dev<float>(c, solver, b, x, n_sys, eps, max_iter, status, iters, (cudaStream_t)stream);
+        return EELS_OK;
+    });
+}
+
+int eels_solve_dev(eels_ctx* c, const eels_opts* o, int n_energy, const double* energy_eV, int n_mat,
+                   const eels_c128* eps_p, const eels_c128* eps_h, int n_beam, const eels_beam* beams,
+                   double* p_eels, double* p_cl, double* p_ext, double* p_abs, eels_c128* p_out,
+                   eels_point_stats* stats, void* stream) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (!o || n_energy <= 0 || n_beam <= 0 || n_mat <= 0 || !energy_eV || !eps_p || !eps_h || !beams || !p_eels)
+            throw Fail{EELS_E_INVALID_ARG, "solve_dev: NULL input or non-positive counts"};
+        require_current_device(c);
+        // every array argument must be device memory of the context's device
+        const void* ptrs[] = {energy_eV, eps_p, eps_h, beams, p_eels, p_cl, p_ext, p_abs, p_out, stats};
+        for (const void* q : ptrs) {
+            if (!q) continue;
+            cudaPointerAttributes at{};
+            if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+                cudaGetLastError();
+                throw Fail{EELS_E_INVALID_ARG, "solve_dev: an array argument is not CUDA memory"};
+            }
+            if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+                throw Fail{EELS_E_INVALID_ARG, "solve_dev: array arguments must be device memory"};
+            if (at.type == cudaMemoryTypeDevice && at.device != c->device)
+                throw Fail{EELS_E_INVALID_ARG, "solve_dev: an array argument lives on another device"};
+        }
+        cudaStream_t caller = (cudaStream_t)stream;
+        const size_t ne = (size_t)n_energy, np = (size_t)n_energy * n_beam;
+        // inputs: read in the caller's stream order
+        std::vector<double> e_h(ne);
+        std::vector<eels_c128> ep_h(ne * n_mat), eh_h(ne);
+        std::vector<eels_beam> b_h(n_beam);
+        CK(cudaMemcpyAsync(e_h.data(), energy_eV, ne * sizeof(double), cudaMemcpyDeviceToHost, caller));
+        CK(cudaMemcpyAsync(ep_h.data(), eps_p, ep_h.size() * sizeof(eels_c128), cudaMemcpyDeviceToHost, caller));
+        CK(cudaMemcpyAsync(eh_h.data(), eps_h, ne * sizeof(eels_c128), cudaMemcpyDeviceToHost, caller));
+        CK(cudaMemcpyAsync(b_h.data(), beams, n_beam * sizeof(eels_beam), cudaMemcpyDeviceToHost, caller));
+        CK(cudaStreamSynchronize(caller));
+        std::vector<double> pe(np), pc(p_cl ? np : 0), px(p_ext ? np : 0), pa(p_abs ? np : 0);
+        std::vector<eels_c128> po(p_out ? np * (size_t)c->N * 3 : 0);
+        std::vector<eels_point_stats> sv(np);
+        const int code = solve_impl(c, o, n_energy, e_h.data(), n_mat, ep_h.data(), eh_h.data(), n_beam, b_h.data(),
+                                    pe.data(), p_cl ? pc.data() : nullptr, p_ext ? px.data() : nullptr,
+                                    p_abs ? pa.data() : nullptr, p_out ? po.data() : nullptr, sv.data());
+        // outputs: written in the caller's stream order; the call returns once they are in place
+        CK(cudaMemcpyAsync(p_eels, pe.data(), np * sizeof(double), cudaMemcpyHostToDevice, caller));
+        if (p_cl) CK(cudaMemcpyAsync(p_cl, pc.data(), np * sizeof(double), cudaMemcpyHostToDevice, caller));
+        if (p_ext) CK(cudaMemcpyAsync(p_ext, px.data(), np * sizeof(double), cudaMemcpyHostToDevice, caller));
+        if (p_abs) CK(cudaMemcpyAsync(p_abs, pa.data(), np * sizeof(double), cudaMemcpyHostToDevice, caller));
+        if (p_out) CK(cudaMemcpyAsync(p_out, po.data(), po.size() * sizeof(eels_c128), cudaMemcpyHostToDevice, caller));
+        if (stats) CK(cudaMemcpyAsync(stats, sv.data(), np * sizeof(eels_point_stats), cudaMemcpyHostToDevice, caller));
+        CK(cudaStreamSynchronize(caller));
+        return code;
+    });
+}
+
 long long eels_kernel_launches(void) { return g_kernel_launches.load(); }
 
 }  // extern "C"
+
+int eels_internal_device(const eels_ctx* c) { return c ? c->device : -1; }
 
 // Launch the prepared operator with caller-provided FFT scratch (used by
 // eels_matvec_dev_noalloc, which owns a fixed array).  Allocates nothing.
@@ -1301,6 +1484,7 @@ int eels_internal_matvec_with_scratch(eels_ctx* c, int precision, const void* x,
         if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
         if (n_sys <= 0 || n_sys > c->op_systems || !x || !y)
             throw Fail{EELS_E_INVALID_ARG, "matvec: n_sys must be in [1, prepared systems]"};
+        require_current_device(c);
         const LatticeDev& L = c->L;
         const size_t elem = precision == EELS_FP64 ? sizeof(double2) : sizeof(float2);
         const size_t need = (size_t)n_sys * 3 * L.My * L.Nx * L.Mz * elem;

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdio>
 
+#include "fft_warp.cuh"
 #include "kernels.h"
 
 namespace eels {
@@ -602,40 +603,24 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
 // (line, lane) patterns of every access hit distinct banks); the block
 // synchronises once per pass.
 // ---------------------------------------------------------------------------
-constexpr int R64_QS = 132;   // transpose tile strides (8-byte units): line -> 4, lane -> 1 (mod 16)
-constexpr int R64_PS = 17;
-constexpr int R64_TILE = 4 * R64_QS;
 constexpr int R64_SLS = 36;   // slab row stride
 
-template <bool INV>
-__device__ __forceinline__ void fft64_warp(float2 (&v)[8], float2* tile, int q, int p, const float2* tw) {
-    Dft<8, INV, float2>::run(v);
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-        float2 w = tw[p * k];
-        if (INV) w.y = -w.y;
-        v[k] = v[k] * w;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) tile[q * R64_QS + p * R64_PS + k] = v[k];
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = tile[q * R64_QS + i * R64_PS + p];
-    __syncwarp();
-    Dft<8, INV, float2>::run(v);
-}
+// Dipole at depth iz of a column whose occupied cells are contiguous:
+// ci = (index of the column's first dipole - its first iz, first iz, last iz + 1).
+__device__ __forceinline__ int col_dip(int4 ci, int iz) { return (iz >= ci.y && iz < ci.z) ? ci.x + iz : -1; }
 
 struct Slab64Smem {
     float2 tw[64];
     float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];   // this system's per-material coefficients
     float2 S[64 * R64_SLS];
     float2 tile[FFT_THREADS / 32][R64_TILE];
+    int4 ci[64];                                 // this slab's column table (contiguous columns)
 };
 
 // HALF: Ny = Nz = 32, so the lattice fills exactly the first half of every
 // 64-point line: the zero padding and the discarded outputs are known at
 // compile time and their arithmetic drops out.
-template <bool HALF>
+template <bool HALF, bool FAST>
 __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, MatvecArgs<float> a) {
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -647,6 +632,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
     const float2* twg = tw_of<float>(L, 1);          // My = Mz = 64: the y and z tables coincide
     if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
     if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+    if (FAST)
+        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
+    const bool one_mat = L.nmat == 1;
     __syncthreads();
     float2* tile = sm.tile[warp];
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
@@ -661,8 +649,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
             const int y = p + 8 * r;
             v[r] = zero;
             if ((HALF ? r < 4 : y < Ny) && iz < Nz) {
-                const int dip = cm[y * Nz + iz];
-                if (dip >= 0) v[r] = xs[dip] * sm.cf[L.mat[dip]];
+                const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
+                if (dip >= 0) v[r] = xs[dip] * (one_mat ? sm.cf[0] : sm.cf[L.mat[dip]]);
             }
         }
         fft64_warp<false>(v, tile, q, p, sm.tw);
@@ -689,7 +677,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, Mat
     }
 }
 
-template <bool HALF>
+template <bool HALF, bool FAST>
 __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, MatvecArgs<float> a, float invM) {
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -705,6 +693,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
         sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
         sm.dg[threadIdx.x] = to_f(a.diag[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
     }
+    if (FAST)
+        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
+    const bool one_mat = L.nmat == 1;
     __syncthreads();
     float2* tile = sm.tile[warp];
     // inverse z transforms of the 64 rows of U, first Nz outputs into S
@@ -739,9 +730,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
         for (int k = 0; k < 8; ++k) {
             const int y = p + 8 * k;
             if (HALF ? k >= 4 : y >= Ny) continue;
-            const int dip = cm[y * Nz + iz];
+            const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
             if (dip < 0) continue;
-            const int m = L.mat[dip];
+            const int m = one_mat ? 0 : L.mat[dip];
             const C xv = xs[dip];
             const C yv = sm.dg[m] * xv - sm.cf[m] * (invM * v[k]);
             ys[dip] = yv;
@@ -775,81 +766,18 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
 // of lane j (m = 2 k2 + h for k = j + 8h + 16 k2): the same (lane, register)
 // <-> index map as the input.  Slab buffer rows of 68 (= 4 mod 16) values.
 // ---------------------------------------------------------------------------
-constexpr int R128_QS = 148;  // transpose tile strides (8-byte units): line -> 4, lane -> 1 (mod 16)
-constexpr int R128_PS = 17;
-constexpr int R128_TILE = 4 * R128_QS;
 constexpr int R128_SLS = 68;
-
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
-    // n = n1 + 4 n2, k = k1 + 4 k2: length-4 DFTs over n2, twiddles w16^(n1 k1), length-4 DFTs over n1
-    float2 a[4][4];
-#pragma unroll
-    for (int n1 = 0; n1 < 4; ++n1) {
-        float2 t[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
-        Dft<4, INV, float2>::run(t);
-#pragma unroll
-        for (int k1 = 0; k1 < 4; ++k1) a[n1][k1] = t[k1];
-    }
-    // w16^(n1 k1) for n1 k1 in {1, 2, 3, 4, 6, 9}: cos/sin of multiples of pi/8
-    const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
-    const float sg = INV ? 1.f : -1.f;
-    auto rot = [&](float2 x, float c, float s) { return make_float2(x.x * c - x.y * s * sg, x.x * s * sg + x.y * c); };
-    a[1][1] = rot(a[1][1], c1, s1);        // w^1
-    a[1][2] = rot(a[1][2], h, h);          // w^2
-    a[1][3] = rot(a[1][3], s1, c1);        // w^3
-    a[2][1] = rot(a[2][1], h, h);          // w^2
-    a[2][2] = rot(a[2][2], 0.f, 1.f);      // w^4
-    a[2][3] = rot(a[2][3], -h, h);         // w^6
-    a[3][1] = rot(a[3][1], s1, c1);        // w^3
-    a[3][2] = rot(a[3][2], -h, h);         // w^6
-    a[3][3] = rot(a[3][3], -c1, -s1);      // w^9
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) {
-        float2 t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
-        Dft<4, INV, float2>::run(t);
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2];
-    }
-}
-
-template <bool INV>
-__device__ __forceinline__ void fft128_warp(float2 (&v)[16], float2* tile, int q, int p, const float2* tw) {
-    dft16<INV>(v);
-#pragma unroll
-    for (int k = 1; k < 16; ++k) {
-        float2 w = tw[p * k];
-        if (INV) w.y = -w.y;
-        v[k] = v[k] * w;
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) tile[q * R128_QS + p * R128_PS + k] = v[k];
-    __syncwarp();
-    float2 a[8], b[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        a[i] = tile[q * R128_QS + i * R128_PS + p];
-        b[i] = tile[q * R128_QS + i * R128_PS + p + 8];
-    }
-    __syncwarp();
-    Dft<8, INV, float2>::run(a);
-    Dft<8, INV, float2>::run(b);
-#pragma unroll
-    for (int k2 = 0; k2 < 8; ++k2) {
-        v[2 * k2] = a[k2];
-        v[2 * k2 + 1] = b[k2];
-    }
-}
 
 struct Slab128Smem {
     float2 tw[128];
     float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];
     float2 S[128 * R128_SLS];
     float2 tile[FFT_THREADS / 32][R128_TILE];
+    int4 ci[64];                                 // this slab's column table (contiguous columns)
 };
 
 // HALF: Ny = Nz = 64 (the lattice fills exactly half of every line).
-template <bool HALF>
+template <bool HALF, bool FAST>
 __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_fwd128(LatticeDev L, MatvecArgs<float> a) {
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -861,6 +789,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_fwd128(LatticeDev L, Ma
     const float2* twg = tw_of<float>(L, 1);          // My = Mz = 128: the y and z tables coincide
     for (int t = threadIdx.x; t < 128; t += blockDim.x) sm.tw[t] = twg[t];
     if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+    if (FAST)
+        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
+    const bool one_mat = L.nmat == 1;
     __syncthreads();
     float2* tile = sm.tile[warp];
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
@@ -875,8 +806,8 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_fwd128(LatticeDev L, Ma
             const int y = p + 8 * r;
             v[r] = zero;
             if ((HALF ? r < 8 : y < Ny) && iz < Nz) {
-                const int dip = cm[y * Nz + iz];
-                if (dip >= 0) v[r] = xs[dip] * sm.cf[L.mat[dip]];
+                const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
+                if (dip >= 0) v[r] = xs[dip] * (one_mat ? sm.cf[0] : sm.cf[L.mat[dip]]);
             }
         }
         fft128_warp<false>(v, tile, q, p, sm.tw);
@@ -903,7 +834,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_fwd128(LatticeDev L, Ma
     }
 }
 
-template <bool HALF>
+template <bool HALF, bool FAST>
 __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_inv128(LatticeDev L, MatvecArgs<float> a, float invM) {
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -919,6 +850,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_inv128(LatticeDev L, Ma
         sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
         sm.dg[threadIdx.x] = to_f(a.diag[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
     }
+    if (FAST)
+        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
+    const bool one_mat = L.nmat == 1;
     __syncthreads();
     float2* tile = sm.tile[warp];
     // inverse z transforms of the 128 rows of U, first Nz outputs into S
@@ -953,9 +887,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_inv128(LatticeDev L, Ma
         for (int m = 0; m < 16; ++m) {
             const int y = p + 8 * m;
             if (HALF ? m >= 8 : y >= Ny) continue;
-            const int dip = cm[y * Nz + iz];
+            const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
             if (dip < 0) continue;
-            const int mt = L.mat[dip];
+            const int mt = one_mat ? 0 : L.mat[dip];
             const C xv = xs[dip];
             const C yv = sm.dg[mt] * xv - sm.cf[mt] * (invM * v[m]);
             ys[dip] = yv;
@@ -1094,12 +1028,20 @@ template <> bool slab64_launch<float>(const LatticeDev& L, const MatvecArgs<floa
     dim3 grid(L.Nx, a.S * 3);
     count_launch();
     const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
-    if (L.Ny == 32 && L.Nz == 32) {
-        if (!inv) k_slab_fwd64<true><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a);
-        else k_slab_inv64<true><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a, invM);
+    const size_t sm = sizeof(Slab64Smem);
+    const bool half = L.Ny == 32 && L.Nz == 32;
+    if (half && L.contig) {
+        if (!inv) k_slab_fwd64<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv64<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    } else if (half) {
+        if (!inv) k_slab_fwd64<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv64<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    } else if (L.contig) {
+        if (!inv) k_slab_fwd64<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv64<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
     } else {
-        if (!inv) k_slab_fwd64<false><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a);
-        else k_slab_inv64<false><<<grid, FFT_THREADS, sizeof(Slab64Smem), st>>>(L, a, invM);
+        if (!inv) k_slab_fwd64<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv64<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
     }
     return true;
 }
@@ -1112,12 +1054,19 @@ template <> bool slab128_launch<float>(const LatticeDev& L, const MatvecArgs<flo
     count_launch();
     const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
     const size_t sm = sizeof(Slab128Smem);
-    if (L.Ny == 64 && L.Nz == 64) {
-        if (!inv) k_slab_fwd128<true><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv128<true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    const bool half = L.Ny == 64 && L.Nz == 64;
+    if (half && L.contig) {
+        if (!inv) k_slab_fwd128<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv128<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    } else if (half) {
+        if (!inv) k_slab_fwd128<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv128<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    } else if (L.contig) {
+        if (!inv) k_slab_fwd128<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv128<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
     } else {
-        if (!inv) k_slab_fwd128<false><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv128<false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+        if (!inv) k_slab_fwd128<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
+        else k_slab_inv128<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
     }
     return true;
 }
@@ -1173,6 +1122,9 @@ template int autotune_xpass<float>(const LatticeDev&, const MatvecArgs<float>&, 
 template int autotune_xpass<double>(const LatticeDev&, const MatvecArgs<double>&, cudaStream_t);
 
 template <typename Rl> static void xpass_any(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st) {
+    if constexpr (sizeof(Rl) == 4) {
+        if (launch_xpass_reg(L, a, st)) return;
+    }
     const int wx = tuned_w<Rl>(L) ? tuned_w<Rl>(L) : pick_xpass_w<Rl>(L);
     if (wx == 32) xpass_launch<Rl, 32>(L, a, st);
     else if (wx == 16) xpass_launch<Rl, 16>(L, a, st);
@@ -1224,14 +1176,22 @@ void prepare_far_kernels();
 void prepare_kernels() {
     prepare_w<float, 8>(); prepare_w<float, 16>(); prepare_w<float, 32>();
     prepare_w<double, 8>(); prepare_w<double, 16>(); prepare_w<double, 32>();
-    allow_smem(k_slab_fwd64<true>);
-    allow_smem(k_slab_fwd64<false>);
-    allow_smem(k_slab_inv64<true>);
-    allow_smem(k_slab_inv64<false>);
-    allow_smem(k_slab_fwd128<true>);
-    allow_smem(k_slab_fwd128<false>);
-    allow_smem(k_slab_inv128<true>);
-    allow_smem(k_slab_inv128<false>);
+    allow_smem(k_slab_fwd64<true, true>);
+    allow_smem(k_slab_fwd64<true, false>);
+    allow_smem(k_slab_fwd64<false, true>);
+    allow_smem(k_slab_fwd64<false, false>);
+    allow_smem(k_slab_inv64<true, true>);
+    allow_smem(k_slab_inv64<true, false>);
+    allow_smem(k_slab_inv64<false, true>);
+    allow_smem(k_slab_inv64<false, false>);
+    allow_smem(k_slab_fwd128<true, true>);
+    allow_smem(k_slab_fwd128<true, false>);
+    allow_smem(k_slab_fwd128<false, true>);
+    allow_smem(k_slab_fwd128<false, false>);
+    allow_smem(k_slab_inv128<true, true>);
+    allow_smem(k_slab_inv128<true, false>);
+    allow_smem(k_slab_inv128<false, true>);
+    allow_smem(k_slab_inv128<false, false>);
     prepare_far_kernels();
 }
 
@@ -1254,7 +1214,7 @@ size_t matvec_smem_bytes(const LatticeDev& L, bool fp64) {
 }
 
 void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, double2* G, double2* Dr64, float2* Dr32,
-                       cudaStream_t st) {
+                       cudaStream_t st, float2* Dx32) {
     const size_t M = (size_t)L.Mx * L.My * L.Mz;
     dim3 g1((unsigned)((M + 255) / 256), n_slot);
     count_launch();
@@ -1266,6 +1226,7 @@ void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, do
     const size_t R = (size_t)L.Hx * L.Hy * L.Hz * 6 * n_slot;
     count_launch();
     k_extract<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(L, n_slot, G, Dr64, Dr32);
+    if (Dx32) launch_dhat_interleave(L, n_slot, Dr64, Dx32, st);
 }
 
 }  // namespace eels

@@ -197,6 +197,20 @@ __global__ void k_qmr_step(KrylovArgs<Rl> k) {
     warp_sum_parts(k.part_b, s, k.nblk, ob);
     if (!lead) return;
     QmrState q = k.qmr[s];
+    // delta_1 = v_1^T v_1 / |v_1|^2 below the rounding floor of the vector
+    // precision: the Lanczos process breaks down at its start (alpha_1 would be
+    // divided by rounding noise and the rotated tau collapse to a false
+    // convergence).  Stop with status 3 and the zero x that k_qmr_scale wrote.
+    const double delta_floor = sizeof(Rl) == 4 ? 1e-5 : 1e-12;
+    if (q.iters == 0 && !(cabs_(q.delta) >= delta_floor)) {
+        q.iters = 1;
+        q.status = 3;
+        k.qmr[s] = q;
+        k.upd[s] = 0;
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+        return;
+    }
     const double2 alpha = cdiv(make_double2(oa[0], oa[1]), q.delta);
     const double rho_n = sqrt(ob[2]);
     // Givens: apply rotations n-2, n-1 to the column (beta_n, alpha_n, rho_{n+1})
@@ -344,8 +358,8 @@ __global__ void k_qmr2_start(KrylovArgs<Rl> k) {
     q.inv_rho = 0.0;
     if (rho > 0.0) {
         q.inv_rho = 1.0 / rho;
-        // v_1^T v_1 ~ 0 is left to the first step's breakdown checks, after
-        // k_qmr2_scale has zeroed x (a system stopped here would keep a stale x)
+        // v_1^T v_1 ~ 0 is caught by the first step, after k_qmr2_scale has
+        // zeroed x (a system stopped here would keep a stale x)
         q.delta = make_double2(o[0] / (rho * rho), o[1] / (rho * rho));
     } else {                        // zero right-hand side: x = 0 is exact
         q.status = 1;
@@ -421,6 +435,20 @@ __global__ void k_qmr2_step(KrylovArgs<Rl> k) {
     warp_sum_parts(k.part_b, s, k.nblk, ob);
     if (!lead) return;
     Qmr2State q = k.qmr2[s];
+    // delta_1 = v_1^T v_1 / |v_1|^2 below the rounding floor of the vector
+    // precision: the Lanczos process breaks down at its start (beta_1 would be
+    // eps_1 / rounding noise, and tau collapse to a false convergence with
+    // x ~ 0).  Stop with status 3 and the zero x that k_qmr2_scale wrote.
+    const double delta_floor = sizeof(Rl) == 4 ? 1e-5 : 1e-12;
+    if (q.iters == 0 && !(cabs_(q.delta) >= delta_floor)) {
+        q.iters = 1;
+        q.status = 3;
+        k.qmr2[s] = q;
+        k.upd[s] = 0;
+        k.active[s] = 0;
+        atomicSub(k.n_active, 1);
+        return;
+    }
     const double2 eps = make_double2(oa[0], oa[1]);
     const double2 beta = cdiv(eps, q.delta);
     const double abeta = cabs_(beta);

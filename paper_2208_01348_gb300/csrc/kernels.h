@@ -28,6 +28,9 @@ struct LatticeDev {
     const uint8_t* mat;           // [N] 0-based material
     const int* dip_cell;          // [N] internal dipole -> cell index ix + Nx (iy + Ny iz)
     const int2* col_range;        // [Ny][Nx] occupied iz range [first, last+1) (first = last = 0 if empty)
+    const int4* colinfo;          // [Nx][Ny] (index of the column's first dipole - first, first, last+1, 0)
+    int contig;                   // 1 if every column's occupied cells are contiguous in z (colinfo is exact)
+    int nmat;                     // materials used by the lattice (1: one coefficient per system)
     FftPlan px, py, pz;
     int xw32, xw64;               // x-pass tile width chosen by the autotuner (0: size heuristic)
     const double2* tw64x; const double2* tw64y; const double2* tw64z;   // exp(-2 pi i t / M)
@@ -49,6 +52,7 @@ struct MatvecArgs {
     const int* active;            // [S] or nullptr
     double* dot_part;             // optional [S][3 Nx][4]: per-slab sum x.y (unconjugated), written by the
                                   // three-pass path's last kernel
+    const float2* Dx;             // FP32 D-hat [slot][Hy][Hz][6][Hx] (register x pass), or nullptr
     int S;
 };
 
@@ -59,7 +63,14 @@ bool launch_matvec(const LatticeDev& L, const MatvecArgs<Rl>& a, cudaStream_t st
 // D-hat build for n_slot energies: kappa[slot] = k d (complex).  G scratch
 // [n_slot][6][My][Mx][Mz] FP64; outputs reduced D-hat FP64 and FP32.
 void launch_dhat_build(const LatticeDev& L, int n_slot, const double2* kappa, double2* Gscratch,
-                       double2* Dr64, float2* Dr32, cudaStream_t st);
+                       double2* Dr64, float2* Dr32, cudaStream_t st, float2* Dx32 = nullptr);
+// FP32 copy Dx[slot][ky][kz][comp][kx] of the octant D-hat (read by the
+// register-resident x pass).
+void launch_dhat_interleave(const LatticeDev& L, int n_slot, const double2* Dr64, float2* Dx, cudaStream_t st);
+// Register-resident x pass (Mx = 64 or 128, FP32): false when the lattice or
+// the arguments do not suit it (the caller then launches the shared-memory one).
+bool xpass_reg_supported(const LatticeDev& L);
+bool launch_xpass_reg(const LatticeDev& L, const MatvecArgs<float>& a, cudaStream_t st);
 
 size_t matvec_smem_bytes(const LatticeDev& L, bool fp64);
 // Times the x pass with every tile width whose shared memory fits, on the

@@ -30,16 +30,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 std::mutex g_mu;
 void* g_scratch_ptr[256] = {};   // device address of g_noalloc_scratch per device ordinal
 
-// Device address of the scratch on the current device: looked up once per
-// device (the first call on that device), with that device current.
-int scratch_address(void** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return EELS_E_CUDA;
+// Device address of the scratch on device `dev` (the context's device):
+// looked up once per device (the first call on that device) with that
+// device made current for the lookup, then the caller's current device is
+// restored.
+int scratch_address(int dev, void** out) {
+    if (dev < 0 || dev >= 256) return EELS_E_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_ptr[dev]) {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) {
+            cudaGetLastError();
+            return EELS_E_CUDA;
+        }
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
+        cudaError_t e = cudaSetDevice(dev);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e2 = cudaSetDevice(cur);
+        if (e != cudaSuccess || e2 != cudaSuccess || !p) {
             cudaGetLastError();
             return EELS_E_CUDA;
         }
@@ -51,9 +59,11 @@ int scratch_address(void** out) {
 
 }  // namespace
 
-// Engine-side helper (engine.cu): validates the context and launches the
-// prepared operator with the given scratch.  Returns an EELS_* code and sets
-// the context's error text on failure.
+// Engine-side helpers (engine.cu): the context's device ordinal, and the
+// launch of the prepared operator with the given scratch (it validates the
+// context, refuses a call whose current device is not the context's, returns
+// an EELS_* code and sets the context's error text on failure).
+int eels_internal_device(const eels_ctx* ctx);
 int eels_internal_matvec_with_scratch(eels_ctx* ctx, int precision, const void* x, void* y, int n_sys, void* stream,
                                       void* scratch, size_t scratch_bytes);
 
@@ -61,7 +71,7 @@ extern "C" int eels_matvec_dev_noalloc(eels_ctx* ctx, int precision, const void*
                                        void* cuda_stream) {
     if (!ctx) return EELS_E_INVALID_ARG;
     void* scratch = nullptr;
-    const int rc = scratch_address(&scratch);
+    const int rc = scratch_address(eels_internal_device(ctx), &scratch);
     if (rc != EELS_OK) return rc;
     return eels_internal_matvec_with_scratch(ctx, precision, x, y, n_sys, cuda_stream, scratch, kScratchBytes);
 }

@@ -111,6 +111,10 @@ _sig = {
     "eels_vacuum_equivalent": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(eels_vacuum_map)]),
     "eels_tile_widths": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
+    "eels_krylov_solve_dev": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_double, C.c_int,
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
+    "eels_solve_dev": (C.c_int, [_P, C.POINTER(eels_opts), C.c_int, _P, C.c_int, _P, _P, C.c_int, _P,
+                                 _P, _P, _P, _P, _P, _P, _P]),
     "eels_server_create": (C.c_int, [C.POINTER(_P), C.POINTER(eels_server_opts)]),
     "eels_server_submit": (C.c_int, [_P, C.POINTER(eels_grid), C.POINTER(eels_opts), C.c_int, _dp, C.c_int, _cp, _cp,
                                      C.c_int, C.POINTER(eels_beam), C.POINTER(C.c_longlong)]),
@@ -345,6 +349,42 @@ def eels_prepare_operator(ctx, energies_eV, eps_p, eps_h) -> None:
 
 def eels_matvec_dev(ctx, precision: int, x_ptr: int, y_ptr: int, n_sys: int, stream: int = 0) -> None:
     _check(_lib.eels_matvec_dev(ctx, precision, _P(x_ptr), _P(y_ptr), n_sys, _P(stream) if stream else None), ctx)
+
+
+def eels_krylov_solve_dev(ctx, precision: int, solver: int, b_ptr: int, x_ptr: int, n_sys: int, eps: float,
+                          max_iter: int, stream: int = 0):
+    """Krylov solve A' x = b on the prepared operator (device vectors [n_sys][3][N]);
+    returns (status, iters) arrays [n_sys] (1 converged, 2 iteration limit, 3 breakdown)."""
+    st = (C.c_int * n_sys)()
+    it = (C.c_int * n_sys)()
+    _check(_lib.eels_krylov_solve_dev(ctx, precision, solver, _P(b_ptr), _P(x_ptr), n_sys, float(eps), int(max_iter),
+                                      st, it, _P(stream) if stream else None), ctx)
+    return np.array(st[:], dtype=int), np.array(it[:], dtype=int)
+
+
+def eels_solve_dev(ctx, opts: eels_opts, energies, eps_p, eps_h, beams, p_eels, p_cl=None, p_ext=None, p_abs=None,
+                   p_out=None, stats=None, stream: int = 0) -> int:
+    """eels_solve on device buffers: every array argument is a torch CUDA
+    tensor (energies float64 [E]; eps_p complex128 [E][n_mat]; eps_h complex128
+    [E]; beams float64 [B][2]; outputs float64 [E][B], p_out complex128
+    [E][B][N][3], stats: a uint8 tensor of E*B*sizeof(eels_point_stats) bytes).
+    Returns the eels_solve code (EELS_OK or EELS_E_NOT_CONVERGED); raises on
+    other errors."""
+    def ptr(t):
+        if t is None:
+            return None
+        if not t.is_contiguous():
+            raise ValueError("eels_solve_dev: tensors must be contiguous")
+        return _P(t.data_ptr())
+    ne = int(energies.numel())
+    n_mat = int(eps_p.numel()) // ne
+    nb = int(beams.numel()) // 2
+    code = _lib.eels_solve_dev(ctx, C.byref(opts), ne, ptr(energies), n_mat, ptr(eps_p), ptr(eps_h), nb, ptr(beams),
+                               ptr(p_eels), ptr(p_cl), ptr(p_ext), ptr(p_abs), ptr(p_out), ptr(stats),
+                               _P(stream) if stream else None)
+    if code not in (EELS_OK, EELS_E_NOT_CONVERGED):
+        _check(code, ctx)
+    return code
 
 
 EELS_NOALLOC_SCRATCH_BYTES = 64 << 20

@@ -82,7 +82,10 @@ def _random_grid(dims, seed, frac=0.7, nmat=1):
 
 
 @pytest.mark.parametrize("dims", [(1, 1, 1), (2, 2, 2), (3, 4, 5), (7, 3, 2), (5, 9, 6), (12, 12, 12), (13, 6, 17),
-                                  (32, 5, 3), (31, 4, 6), (64, 3, 2)])
+                                  (32, 5, 3), (31, 4, 6), (64, 3, 2),
+                                  # padded x lengths 64 and 128 with Mz a multiple of 16 / 8: the
+                                  # register-resident FP32 x pass (full and ragged x lines)
+                                  (32, 3, 8), (31, 5, 8), (64, 2, 4), (64, 3, 8)])
 def test_matvec_equals_dense_oracle(dd, ctx, dims):
     nx, ny, nz = dims
     nmat = 2 if nx * ny * nz > 8 else 1
@@ -102,7 +105,8 @@ def test_matvec_equals_dense_oracle(dd, ctx, dims):
         assert rel(y32[i], ref[i]) < 2e-5
 
 
-@pytest.mark.parametrize("dims", [(4, 32, 31), (3, 31, 32), (6, 32, 32), (2, 64, 64), (3, 64, 64)])
+@pytest.mark.parametrize("dims", [(4, 32, 31), (3, 31, 32), (6, 32, 32), (2, 64, 64), (3, 64, 64), (32, 32, 32),
+                                  (31, 32, 30), (64, 12, 24), (64, 64, 64)])
 def test_matvec_64_point_transforms_equal_fft_oracle(dd, ctx, dims):
     """Lattices whose y and z transforms are 64 or 128 points long (the FP32
     path then uses the register-resident slab kernels); the oracle is its own
@@ -111,7 +115,8 @@ def test_matvec_64_point_transforms_equal_fft_oracle(dd, ctx, dims):
     occ = _random_grid(dims, seed=7 * nx + ny + nz, nmat=2)
     d_nm = 1.5
     dd.eels_set_grid(ctx, occ, d_nm)
-    assert dd.eels_padded_dims(ctx)[1:] in ((64, 64), (128, 128))
+    mx, my, mz = dd.eels_padded_dims(ctx)
+    assert (my, mz) in ((64, 64), (128, 128)) or mx in (64, 128)
     eps_p = [I.drude(2.0), 2.5 + 0.3j]
     eps_h = 2.1025 + 0j
     pt = run.setup(nx, ny, nz, d_nm, occ, 2.0, eps_p, eps_h, (100.0, 100.0), ekin_keV=120.0)
@@ -123,6 +128,31 @@ def test_matvec_64_point_transforms_equal_fft_oracle(dd, ctx, dims):
     for i in range(2):
         assert rel(y64[i], ref[i]) < 1e-12
         assert rel(y32[i], ref[i]) < 2e-5
+
+
+@pytest.mark.parametrize("n,two_mat", [(32, False), (32, True), (64, False), (64, True), (31, True)])
+def test_matvec_sphere_lattices_equal_fft_oracle(dd, ctx, n, two_mat):
+    """Sphere lattices (every column's occupied cells contiguous: the slab
+    kernels address dipoles through the per-column table), with one material
+    or a core and shell of two, at the padded sizes of the 64- and 128-point
+    register kernels; the oracle is its own FFT convolution."""
+    occ = I.sphere_occupancy(n, 1.0 * n)
+    if two_mat:
+        c = (np.arange(n) + 0.5) - n / 2.0
+        z, y, x = np.meshgrid(c, c, c, indexing="ij")
+        occ = np.where(x * x + y * y + z * z <= (0.3 * n) ** 2, 2, occ).astype(np.uint8)
+    d_nm = 1.0
+    dd.eels_set_grid(ctx, occ, d_nm)
+    eps_p = [I.drude(2.0), 2.5 + 0.3j][:2 if two_mat else 1]
+    eps_h = 4.0 + 0.05j
+    pt = run.setup(n, n, n, d_nm, occ, 2.0, eps_p, eps_h, (100.0, 100.0), ekin_keV=200.0)
+    op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha)
+    x = I.random_complex((1, len(pt.r), 3), seed=13)
+    ref = op.matvec(x[0])
+    y32 = dd.eels_apply_matrix(ctx, dd.EELS_MIXED, 2.0, eps_p, eps_h, x)
+    y64 = dd.eels_apply_matrix(ctx, dd.EELS_FP64, 2.0, eps_p, eps_h, x)
+    assert rel(y64[0], ref) < 1e-12
+    assert rel(y32[0], ref) < 2e-5
 
 
 # ------------------------------------------------------------------ solve
@@ -400,3 +430,129 @@ def test_vacuum_equivalent_problems_reproduce_host_probabilities(dd, ctx):
         for a, b in ((vac.p_eels, host.p_eels), (vac.p_cl, host.p_cl), (vac.p_ext, host.p_ext),
                      (vac.p_abs, host.p_abs)):
             assert np.allclose(maps[0]["p_scale"] * a, b, rtol=1e-9, atol=0), rule
+
+
+# ------------------------------------------------------------------ Krylov solve on the prepared operator
+def _scaled_operator(pt):
+    """A' = a^1/2 (alpha~^-1 - G~) a^1/2 d^3 with a = alpha~ / d^3 (lattice units),
+    the operator eels_prepare_operator sets up, in the oracle's dipole order."""
+    A = green.dense_matrix(pt.r, pt.k, pt.alpha)
+    sa = np.repeat(np.sqrt(pt.alpha / pt.d ** 3), 3)
+    return sa[:, None] * A * sa[None, :] * pt.d ** 3
+
+
+def _internal_perm(pt):
+    """internal dipole i (cells sorted by ix, iy, iz) -> oracle dipole (x-fastest order)."""
+    idx = pt.idx
+    return np.lexsort((idx[:, 2], idx[:, 1], idx[:, 0]))
+
+
+def _to_internal(v, perm):       # [N][3] oracle order -> [3][N] internal order
+    return np.ascontiguousarray(v[perm].T)
+
+
+def _from_internal(v, perm):     # [3][N] internal -> [N][3] oracle order
+    out = np.empty((v.shape[1], 3), dtype=v.dtype)
+    out[perm] = v.T
+    return out
+
+
+@pytest.mark.parametrize("solver", ["QMR2", "QMR", "BICGSTAB"])
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_krylov_solve_dev_matches_dense_solve(dd, ctx, solver, prec):
+    """eels_krylov_solve_dev on the prepared operator against LU of the same
+    Jacobi-scaled matrix (oracle dense assembly), for a random right-hand side."""
+    import torch
+    dims = (6, 5, 7)
+    occ = _random_grid(dims, seed=41, nmat=2)
+    d_nm, e_eV = 2.0, 2.3
+    eps_p, eps_h = [I.drude(e_eV), 3.0 + 0.4j], 2.0 + 0.1j
+    dd.eels_set_grid(ctx, occ, d_nm)
+    dd.eels_prepare_operator(ctx, [e_eV], [eps_p], [eps_h])
+    pt = run.setup(*dims, d_nm, occ, e_eV, eps_p, eps_h, (100.0, 100.0), ekin_keV=100.0)
+    perm = _internal_perm(pt)
+    b = I.random_complex((len(pt.r), 3), seed=17)
+    ref = np.linalg.solve(_scaled_operator(pt), b.reshape(-1)).reshape(-1, 3)
+    dt = torch.complex128 if prec == "FP64" else torch.complex64
+    bt = torch.from_numpy(_to_internal(b, perm)).to(dt).cuda()
+    xt = torch.zeros_like(bt)
+    eps = 1e-12 if prec == "FP64" else 1e-6
+    status, iters = dd.eels_krylov_solve_dev(ctx, getattr(dd, "EELS_" + prec), getattr(dd, "EELS_" + solver),
+                                             bt.data_ptr(), xt.data_ptr(), 1, eps, 5000,
+                                             torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert status[0] == 1 and iters[0] > 0
+    x = _from_internal(xt.cpu().numpy().astype(np.complex128), perm)
+    assert rel(x, ref) < (1e-9 if prec == "FP64" else 1e-4)
+
+
+@pytest.mark.parametrize("solver", ["QMR2", "QMR"])
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_qmr_reports_breakdown_when_b_transpose_b_vanishes(dd, ctx, solver, prec):
+    """b = u + i w with u orthogonal to w and |u| = |w| has b^T b = 0: the
+    complex-symmetric Lanczos process breaks down at its start.  The solver
+    must report a breakdown (status 3) with x = 0, not a convergence."""
+    import torch
+    dims = (6, 5, 7)
+    occ = _random_grid(dims, seed=41, nmat=2)
+    d_nm, e_eV = 2.0, 2.3
+    eps_p, eps_h = [I.drude(e_eV), 3.0 + 0.4j], 2.0 + 0.1j
+    dd.eels_set_grid(ctx, occ, d_nm)
+    dd.eels_prepare_operator(ctx, [e_eV], [eps_p], [eps_h])
+    n = dd.eels_num_dipoles(ctx)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(3 * n)
+    w = rng.standard_normal(3 * n)
+    w -= (w @ u) / (u @ u) * u
+    w *= np.linalg.norm(u) / np.linalg.norm(w)
+    b = (u + 1j * w).reshape(3, n)
+    assert abs(np.sum(b * b)) < 1e-12 * np.sum(np.abs(b) ** 2)
+    dt = torch.complex128 if prec == "FP64" else torch.complex64
+    bt = torch.from_numpy(b).to(dt).cuda()
+    xt = torch.full_like(bt, 7.0)
+    status, iters = dd.eels_krylov_solve_dev(ctx, getattr(dd, "EELS_" + prec), getattr(dd, "EELS_" + solver),
+                                             bt.data_ptr(), xt.data_ptr(), 1, 1e-6, 100,
+                                             torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert status[0] == 3 and iters[0] == 1
+    assert torch.count_nonzero(xt).item() == 0
+
+
+# ------------------------------------------------------------------ device-buffer solve
+def test_solve_dev_is_bit_identical_to_host_solve(dd, ctx):
+    """eels_solve_dev with torch device buffers and the current stream gives
+    the same bits as eels_solve with host buffers."""
+    import ctypes
+    import torch
+    w = I.config_small_sphere()
+    g = w.grid
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    energies = np.array([2.0, 2.4, 2.9])
+    eps_p = np.array([[I.drude(e)] for e in energies])
+    eps_h = np.full(len(energies), 1.0 + 0j)
+    beams = np.array([[15.0, 0.0], [0.0, 13.0]])
+    o = dd.eels_default_opts(ekin_keV=w.ekin_keV, eps_it=1e-8)
+    host = dd.eels_solve(ctx, o, energies, eps_p, eps_h, beams, want_p=True)
+    dev = dict(device="cuda")
+    ne, nb, n = len(energies), len(beams), dd.eels_num_dipoles(ctx)
+    et = torch.tensor(energies, dtype=torch.float64, **dev)
+    ept = torch.tensor(eps_p, dtype=torch.complex128, **dev)
+    eht = torch.tensor(eps_h, dtype=torch.complex128, **dev)
+    bt = torch.tensor(beams, dtype=torch.float64, **dev)
+    out = {k: torch.zeros(ne, nb, dtype=torch.float64, **dev) for k in ("eels", "cl", "ext", "abs")}
+    pt = torch.zeros(ne, nb, n, 3, dtype=torch.complex128, **dev)
+    st = torch.zeros(ne * nb * ctypes.sizeof(dd.eels_point_stats), dtype=torch.uint8, **dev)
+    code = dd.eels_solve_dev(ctx, o, et, ept, eht, bt, out["eels"], out["cl"], out["ext"], out["abs"], pt, st,
+                             stream=torch.cuda.current_stream().cuda_stream)
+    assert code == dd.EELS_OK
+    assert np.array_equal(out["eels"].cpu().numpy(), host.p_eels)
+    assert np.array_equal(out["cl"].cpu().numpy(), host.p_cl)
+    assert np.array_equal(out["ext"].cpu().numpy(), host.p_ext)
+    assert np.array_equal(out["abs"].cpu().numpy(), host.p_abs)
+    assert np.array_equal(pt.cpu().numpy(), host.p)
+    sts = (dd.eels_point_stats * (ne * nb)).from_buffer_copy(st.cpu().numpy().tobytes())
+    assert [s.iters for s in sts] == host.iters.ravel().tolist()
+    # a host buffer where device memory is required is refused before any work
+    with pytest.raises(dd.EelsError) as e:
+        dd.eels_solve_dev(ctx, o, et.cpu(), ept, eht, bt, out["eels"])
+    assert e.value.code == dd.EELS_E_INVALID_ARG
