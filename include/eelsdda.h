@@ -231,10 +231,12 @@ int eels_apply_matrix(eels_ctx* ctx, int precision, double energy_eV, int n_mat,
                       eels_c128 eps_h, int n_vec, const eels_c128* x, eels_c128* y);
 
 /* Prepare the Jacobi-scaled operator A' = I - a^1/2 G~' a^1/2 (lattice
- * units: lengths in d, a = alpha~/d^3) for one system per energy, so that
+ * units: lengths in d, a = alpha~/d^3) for one system per entry, so that
  * eels_matvec_dev can apply it.  Builds D-hat (FFT of the Green's tensor,
- * Eq. 5, on the padded lattice) in FP64 and FP32.  Host inputs as in
- * eels_solve (eps_p [n_energy][n_mat]). */
+ * Eq. 5, on the padded lattice) in FP64 and FP32; consecutive entries with
+ * identical energy and permittivities (the beams of one energy) share one
+ * D-hat, which the FFT x pass then reads once for up to 16 of them.  Host
+ * inputs as in eels_solve (eps_p [n_energy][n_mat]). */
 int eels_prepare_operator(eels_ctx* ctx, int n_energy, const double* energy_eV, int n_mat, const eels_c128* eps_p,
                           const eels_c128* eps_h);
 

@@ -106,6 +106,16 @@ int good_fft_len(int n) {
     }
 }
 
+// Padded length along x: 64 or 128 when that embeds the lattice (the
+// register-resident x pass runs those lengths), else the smallest even
+// 7-smooth length (any M >= 2n - 1 embeds the convolution).
+int pad_len_x(int n) {
+    const int need = 2 * n - 1;
+    if (need > 32 && need <= 64) return 64;
+    if (need > 64 && need <= 128) return 128;
+    return good_fft_len(n);
+}
+
 FftPlan make_plan(int L) {
     FftPlan p{};
     p.L = L;
@@ -244,6 +254,9 @@ struct eels_ctx {
     long long graph_kernels = 0;
     // operator prepared by eels_prepare_operator
     int op_systems = 0;
+    // consecutive systems that share a D-hat slot (the beams of one energy):
+    // the x pass reuses a staged D-hat tile over up to this many of them
+    int spb = 1;
 
     std::vector<DevBuf*> buffers() {
         std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &colinfo, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
@@ -315,7 +328,7 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
                 c->dip_cell_h.push_back((int)cell);
                 c->mat_h.push_back((uint8_t)(g->occ[cell] - 1));
             }
-    const int Mx = good_fft_len(nx), My = good_fft_len(ny), Mz = good_fft_len(nz);
+    const int Mx = pad_len_x(nx), My = good_fft_len(ny), Mz = good_fft_len(nz);
     if (Mx > 256 || My > 256 || Mz > 256)
         throw Fail{EELS_E_UNSUPPORTED, "grid: padded FFT length above 256 (extent above 128 cells)"};
     std::vector<int2> cr((size_t)nx * ny, make_int2(0, 0));
@@ -586,6 +599,7 @@ MatvecArgs<Rl> mv_args(eels_ctx* c, int S, const cx<Rl>* x, cx<Rl>* y, const cx<
     a.active = active;
     a.Dx = sizeof(Rl) == 4 ? c->Dx32.as<float2>() : nullptr;
     a.S = S;
+    a.spb = c->spb;
     (void)scaled;
     return a;
 }
@@ -614,7 +628,8 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
                                     (const void*)(size_t)S, (const void*)(size_t)sizeof(Rl),
                                     (const void*)(size_t)inner_cap(o, sizeof(Rl) == 4), c->coef.p, c->diag.p, c->slot.p, c->qmr.p,
                                     c->part_a.p, c->part_b.p, c->active.p, c->upd.p, c->counters.p, c->eps_sys.p,
-                                    c->cellmap.p, c->bicg.p, (const void*)(size_t)o->solver};
+                                    c->cellmap.p, c->bicg.p, (const void*)(size_t)o->solver,
+                                    (const void*)(size_t)c->spb, c->Dx32.p};
     // eps is read inside the step kernel from the kernel argument: make it part of the key
     double epsv = eps;
     const void* ek;
@@ -890,6 +905,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
     for (int e = 0; e < n_energy; ++e)
         ep[e] = energy_params(o->ekin_keV, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m);
     const bool fp64 = o->precision == EELS_FP64;
+    const unsigned timeouts0 = wait_timeouts();
     // far-field directions
     std::vector<double> dirs_h, wts_h;
     if (p_cl) {
@@ -916,6 +932,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
     }
     S_max = std::min(S_max, 21000);
     const int n_sys = n_energy * n_beam;
+    c->spb = std::max(1, std::min(n_beam, 16));
     std::vector<int> iters(n_sys, 0), refin(n_sys, 0);
     std::vector<double> resid(n_sys, 0.0);
     bool all_conv = true;
@@ -1066,6 +1083,8 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
             }
         }
     }
+    if (wait_timeouts() != timeouts0)
+        throw Fail{EELS_E_TIMEOUT, "a bounded device-side wait expired: results of this solve are incomplete"};
     return all_conv ? EELS_OK : EELS_E_NOT_CONVERGED;
 }
 
@@ -1211,7 +1230,7 @@ int eels_query_footprint(const eels_grid* g, const eels_opts* o, int n_systems, 
     size_t n = 0;
     for (size_t i = 0; i < (size_t)g->nx * g->ny * g->nz; ++i) n += g->occ[i] != 0;
     L.N = (int)n;
-    L.Mx = good_fft_len(g->nx); L.My = good_fft_len(g->ny); L.Mz = good_fft_len(g->nz);
+    L.Mx = pad_len_x(g->nx); L.My = good_fft_len(g->ny); L.Mz = good_fft_len(g->nz);
     L.Hx = L.Mx / 2 + 1; L.Hy = L.My / 2 + 1; L.Hz = L.Mz / 2 + 1;
     const size_t Mfull = (size_t)L.Mx * L.My * L.Mz;
     *bytes = (size_t)n_systems * (per_system_bytes(L, o->precision == EELS_FP64) + per_slot_bytes(L)) +
@@ -1297,6 +1316,7 @@ int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, c
         for (int s = 0; s < S; ++s)
             for (int m = 0; m < EELS_MAX_MAT; ++m) diag[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? d2(p.alpha_inv[m]) : make_double2(0, 0);
         std::vector<int> slot(S, 0);
+        c->spb = std::min(S, 16);
         h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->slot, slot, st);
         std::vector<double2> xh((size_t)S * n3);
         for (int s = 0; s < S; ++s)
@@ -1356,18 +1376,28 @@ int eels_prepare_operator(eels_ctx* c, int n_energy, const double* energy_eV, in
         c->Dx32.ensure(S * hs * sizeof(float2));
         const size_t gslot = (size_t)6 * L.Mx * L.My * L.Mz * sizeof(double2);
         c->G.ensure(gslot);
-        std::vector<double2> kap(S), coef((size_t)S * EELS_MAX_MAT), diag((size_t)S * EELS_MAX_MAT, make_double2(1, 0));
+        std::vector<double2> kap, coef((size_t)S * EELS_MAX_MAT), diag((size_t)S * EELS_MAX_MAT, make_double2(1, 0));
         std::vector<int> slot(S);
+        // consecutive systems with the same energy and permittivities share one
+        // D-hat slot (the beams of one energy)
+        int run = 0, max_run = 1;
         for (int e = 0; e < S; ++e) {
             EnergyPar p = energy_params(100.0, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m);
-            kap[e] = d2(p.kappa);
-            slot[e] = e;
+            const bool same = e > 0 && energy_eV[e] == energy_eV[e - 1] && eps_h[e].re == eps_h[e - 1].re &&
+                              eps_h[e].im == eps_h[e - 1].im &&
+                              std::memcmp(eps_p + (size_t)e * n_mat, eps_p + (size_t)(e - 1) * n_mat,
+                                          n_mat * sizeof(eels_c128)) == 0;
+            if (!same) kap.push_back(d2(p.kappa));
+            run = same ? run + 1 : 1;
+            max_run = std::max(max_run, run);
+            slot[e] = (int)kap.size() - 1;
             for (int m = 0; m < EELS_MAX_MAT; ++m) coef[(size_t)e * EELS_MAX_MAT + m] = m < n_mat ? d2(p.sa[m]) : make_double2(0, 0);
         }
         h2d(c->kappa_slot, kap, st);
-        for (int e = 0; e < S; ++e)
+        for (size_t e = 0; e < kap.size(); ++e)
             launch_dhat_build(L, 1, c->kappa_slot.as<double2>() + e, c->G.as<double2>(), c->Dr64.as<double2>() + e * hs,
                               c->Dr32.as<float2>() + e * hs, st, c->Dx32.as<float2>() + e * hs);
+        c->spb = std::min(max_run, 16);
         h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->slot, slot, st);
         c->U.ensure((size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(double2));
         CK(cudaStreamSynchronize(st));

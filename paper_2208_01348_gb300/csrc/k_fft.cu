@@ -590,105 +590,122 @@ __global__ void __launch_bounds__(FFT_THREADS) k_slab_inv(LatticeDev L, MatvecAr
 }
 
 // ---------------------------------------------------------------------------
-// Fused slab passes for My = Mz = 64 in FP32, register resident.
+// Fused slab passes for My = Mz = L = 64 or 128 in FP32, register resident.
 //
-// A warp transforms 4 lines at once: lane = q + 4p holds, for its line q, the
-// elements p + 8r (r = 0..7) of the 64-point line.  A length-8 DFT over the
-// lane's registers, the twiddles exp(-+2 pi i p k / 64), a transpose among the
-// 8 lanes of the line (through a warp-private shared tile) and a second
-// length-8 DFT leave element j + 8k of the transform in register k of lane
-// j: input and output use the same (lane, register) <-> index map, forward
-// and inverse alike.  Between the y and the z transforms the slab
-// S[64][Nz] sits in shared memory (row stride 36 = 4 mod 16: the 4 x 4
-// (line, lane) patterns of every access hit distinct banks); the block
-// synchronises once per pass.
+// A warp transforms 4 lines at once (fft_warp.cuh): lane = q + 4p holds, for
+// its line q, the elements p + 8r (r < R = L/8) of the line, and the
+// transform leaves element j + 8m in register m of lane j.  Between the y and
+// the z transforms the slab S[L][Nz] sits in shared memory (row stride
+// 4 mod 16: the 4 x 4 (line, lane) patterns of every access hit distinct
+// banks); the block synchronises once per pass.  Every loop over line quads
+// loads the next quad's inputs before transforming the current one, so the
+// global loads of one quad overlap the arithmetic of the previous one.
+// HALF: Ny = Nz = L/2 (the lattice fills exactly half of every line): the
+// zero padding and the discarded outputs are known at compile time.  FAST:
+// every column's occupied cells are contiguous in z, so a dipole's index is
+// the column's base plus iz (no cell-map load).
 // ---------------------------------------------------------------------------
-constexpr int R64_SLS = 36;   // slab row stride
-
 // Dipole at depth iz of a column whose occupied cells are contiguous:
 // ci = (index of the column's first dipole - its first iz, first iz, last iz + 1).
 __device__ __forceinline__ int col_dip(int4 ci, int iz) { return (iz >= ci.y && iz < ci.z) ? ci.x + iz : -1; }
 
-struct Slab64Smem {
-    float2 tw[64];
-    float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];   // this system's per-material coefficients
-    float2 S[64 * R64_SLS];
-    float2 tile[FFT_THREADS / 32][R64_TILE];
-    int4 ci[64];                                 // this slab's column table (contiguous columns)
+template <int R> struct SlabR {
+    static constexpr int L = 8 * R;
+    static constexpr int SLS = R == 8 ? 36 : 68;           // slab row stride
+    static constexpr int TILE = R == 8 ? R64_TILE : R128_TILE;
 };
 
-// HALF: Ny = Nz = 32, so the lattice fills exactly the first half of every
-// 64-point line: the zero padding and the discarded outputs are known at
-// compile time and their arithmetic drops out.
-template <bool HALF, bool FAST>
-__global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_fwd64(LatticeDev L, MatvecArgs<float> a) {
+template <int R> struct SlabRSmem {
+    float2 tw2[(R - 1) * 8];                     // exp(-2 pi i p k / L) at [k - 1][p]: conflict-free per k
+    float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];   // this system's per-material coefficients
+    float2 S[SlabR<R>::L * SlabR<R>::SLS];
+    float2 tile[FFT_THREADS / 32][SlabR<R>::TILE];
+    int4 ci[SlabR<R>::L / 2];                    // this slab's column table (contiguous columns)
+};
+
+template <int R, bool HALF, bool FAST>
+__global__ void __launch_bounds__(FFT_THREADS, R == 8 ? 4 : 2) k_slab_fwd_r(LatticeDev L, MatvecArgs<float> a) {
     using C = float2;
+    using P = SlabR<R>;
+    constexpr int LEN = P::L, SLS = P::SLS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Slab64Smem& sm = *reinterpret_cast<Slab64Smem*>(smem_raw);
+    SlabRSmem<R>& sm = *reinterpret_cast<SlabRSmem<R>*>(smem_raw);
     const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
     const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
     const int nwarp = blockDim.x >> 5;
-    const float2* twg = tw_of<float>(L, 1);          // My = Mz = 64: the y and z tables coincide
-    if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
+    const float2* twg = tw_of<float>(L, 1);          // My = Mz: the y and z tables coincide
+    for (int t = threadIdx.x; t < (R - 1) * 8; t += blockDim.x) sm.tw2[t] = twg[(t & 7) * ((t >> 3) + 1)];
     if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
     if (FAST)
         for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
     const bool one_mat = L.nmat == 1;
     __syncthreads();
     float2* tile = sm.tile[warp];
+    auto tw = [&](int k) { return sm.tw2[(k - 1) * 8 + p]; };
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
     const C zero = make_float2(0.f, 0.f);
+    const int stride = nwarp * 4;
     // y transforms of the Nz columns, 4 per warp: gathered from x, into S
-    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
+    auto gather = [&](int iz0, C (&v)[R]) {
         const int iz = iz0 + q;
-        C v[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int y = p + 8 * r;
             v[r] = zero;
-            if ((HALF ? r < 4 : y < Ny) && iz < Nz) {
+            if ((HALF ? r < R / 2 : y < Ny) && iz < Nz) {
                 const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
                 if (dip >= 0) v[r] = xs[dip] * (one_mat ? sm.cf[0] : sm.cf[L.mat[dip]]);
             }
         }
-        fft64_warp<false>(v, tile, q, p, sm.tw);
+    };
+    C vn[R];
+    if (warp * 4 < Nz) gather(warp * 4, vn);
+    for (int iz0 = warp * 4; iz0 < Nz; iz0 += stride) {
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = vn[r];
+        if (iz0 + stride < Nz) gather(iz0 + stride, vn);
+        fft_warp_t<R, false, HALF>(v, tile, q, p, tw);
+        const int iz = iz0 + q;
         if (iz < Nz) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) sm.S[(p + 8 * k) * R64_SLS + iz] = v[k];
+            for (int m = 0; m < R; ++m) sm.S[(p + 8 * m) * SLS + iz] = v[m];
         }
     }
     __syncthreads();
-    // z transforms of the 64 rows, 4 per warp: from S, written to U
-    C* U = a.U + (((size_t)s * 3 + c) * 64 * L.Nx + ix) * 64;
-    const size_t row = (size_t)L.Nx * 64;
-    for (int ky0 = warp * 4; ky0 < 64; ky0 += nwarp * 4) {
+    // z transforms of the LEN rows, 4 per warp: from S, written to U
+    C* U = a.U + (((size_t)s * 3 + c) * LEN * L.Nx + ix) * LEN;
+    const size_t row = (size_t)L.Nx * LEN;
+    for (int ky0 = warp * 4; ky0 < LEN; ky0 += stride) {
         const int ky = ky0 + q;
-        C v[8];
+        C v[R];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < R; ++r) {
             const int z = p + 8 * r;
-            v[r] = (HALF ? r < 4 : z < Nz) ? sm.S[ky * R64_SLS + z] : zero;
+            v[r] = (HALF ? r < R / 2 : z < Nz) ? sm.S[ky * SLS + z] : zero;
         }
-        fft64_warp<false>(v, tile, q, p, sm.tw);
+        fft_warp_t<R, false, HALF>(v, tile, q, p, tw);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) U[(size_t)ky * row + p + 8 * k] = v[k];
+        for (int m = 0; m < R; ++m) U[(size_t)ky * row + p + 8 * m] = v[m];
     }
 }
 
-template <bool HALF, bool FAST>
-__global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, MatvecArgs<float> a, float invM) {
+template <int R, bool HALF, bool FAST>
+__global__ void __launch_bounds__(FFT_THREADS, R == 8 ? 4 : 2) k_slab_inv_r(LatticeDev L, MatvecArgs<float> a, float invM) {
     using C = float2;
+    using P = SlabR<R>;
+    constexpr int LEN = P::L, SLS = P::SLS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Slab64Smem& sm = *reinterpret_cast<Slab64Smem*>(smem_raw);
+    SlabRSmem<R>& sm = *reinterpret_cast<SlabRSmem<R>*>(smem_raw);
     __shared__ float red[2 * FFT_THREADS / 32];
     const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
     if (a.active && !a.active[s]) return;
     const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
     const int nwarp = blockDim.x >> 5;
     const float2* twg = tw_of<float>(L, 2);
-    if (threadIdx.x < 64) sm.tw[threadIdx.x] = twg[threadIdx.x];
+    for (int t = threadIdx.x; t < (R - 1) * 8; t += blockDim.x) sm.tw2[t] = twg[(t & 7) * ((t >> 3) + 1)];
     if (threadIdx.x < EELS_MAX_MAT) {
         sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
         sm.dg[threadIdx.x] = to_f(a.diag[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
@@ -698,206 +715,65 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_slab_inv64(LatticeDev L, Mat
     const bool one_mat = L.nmat == 1;
     __syncthreads();
     float2* tile = sm.tile[warp];
-    // inverse z transforms of the 64 rows of U, first Nz outputs into S
-    const C* U = a.U + (((size_t)s * 3 + c) * 64 * L.Nx + ix) * 64;
-    const size_t row = (size_t)L.Nx * 64;
-    for (int ky0 = warp * 4; ky0 < 64; ky0 += nwarp * 4) {
+    auto tw = [&](int k) { return sm.tw2[(k - 1) * 8 + p]; };
+    const int stride = nwarp * 4;
+    // inverse z transforms of the LEN rows of U, first Nz outputs into S
+    const C* U = a.U + (((size_t)s * 3 + c) * LEN * L.Nx + ix) * LEN;
+    const size_t row = (size_t)L.Nx * LEN;
+    C vn[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) vn[r] = U[(size_t)(warp * 4 + q) * row + p + 8 * r];
+    for (int ky0 = warp * 4; ky0 < LEN; ky0 += stride) {
         const int ky = ky0 + q;
-        C v[8];
+        C v[R];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = U[(size_t)ky * row + p + 8 * r];
-        fft64_warp<true>(v, tile, q, p, sm.tw);
+        for (int r = 0; r < R; ++r) v[r] = vn[r];
+        if (ky0 + stride < LEN) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int z = p + 8 * k;
-            if (HALF ? k < 4 : z < Nz) sm.S[ky * R64_SLS + z] = v[k];
+            for (int r = 0; r < R; ++r) vn[r] = U[(size_t)(ky + stride) * row + p + 8 * r];
+        }
+        fft_warp_t<R, true, false>(v, tile, q, p, tw);
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            const int z = p + 8 * m;
+            if (HALF ? m < R / 2 : z < Nz) sm.S[ky * SLS + z] = v[m];
         }
     }
     __syncthreads();
-    // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
+    // inverse y transforms of the Nz columns, first Ny outputs combined with x
+    // and scattered; each lane loads its x values before its transform
     const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
     C* ys = a.y + ((size_t)s * 3 + c) * L.N;
     const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+    constexpr int RO = HALF ? R / 2 : R;             // registers that can hold lattice rows
     float dot0 = 0.f, dot1 = 0.f;
-    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
+    for (int iz0 = warp * 4; iz0 < Nz; iz0 += stride) {
         const int iz = iz0 + q;
-        C v[8];
+        int dip[RO];
+        C xv[RO];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = iz < Nz ? sm.S[(p + 8 * r) * R64_SLS + iz] : make_float2(0.f, 0.f);
-        fft64_warp<true>(v, tile, q, p, sm.tw);
-        if (iz >= Nz) continue;
+        for (int m = 0; m < RO; ++m) {
+            const int y = p + 8 * m;
+            dip[m] = -1;
+            if (iz < Nz && (HALF || y < Ny)) dip[m] = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
+            xv[m] = dip[m] >= 0 ? xs[dip[m]] : make_float2(0.f, 0.f);
+        }
+        C v[R];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int y = p + 8 * k;
-            if (HALF ? k >= 4 : y >= Ny) continue;
-            const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
-            if (dip < 0) continue;
-            const int m = one_mat ? 0 : L.mat[dip];
-            const C xv = xs[dip];
-            const C yv = sm.dg[m] * xv - sm.cf[m] * (invM * v[k]);
-            ys[dip] = yv;
-            dot0 += xv.x * yv.x - xv.y * yv.y;
-            dot1 += xv.x * yv.y + xv.y * yv.x;
+        for (int r = 0; r < R; ++r) v[r] = iz < Nz ? sm.S[(p + 8 * r) * SLS + iz] : make_float2(0.f, 0.f);
+        fft_warp_t<R, true, false>(v, tile, q, p, tw);
+#pragma unroll
+        for (int m = 0; m < RO; ++m) {
+            if (dip[m] < 0) continue;
+            const int mt = one_mat ? 0 : L.mat[dip[m]];
+            const C yv = sm.dg[mt] * xv[m] - sm.cf[mt] * (invM * v[m]);
+            ys[dip[m]] = yv;
+            dot0 += xv[m].x * yv.x - xv[m].y * yv.y;
+            dot1 += xv[m].x * yv.y + xv[m].y * yv.x;
         }
     }
     if (a.dot_part) {
         // block sum in a fixed order (warp shuffles, then thread 0 over the warps)
-        for (int o = 16; o > 0; o >>= 1) {
-            dot0 += __shfl_xor_sync(0xffffffffu, dot0, o);
-            dot1 += __shfl_xor_sync(0xffffffffu, dot1, o);
-        }
-        if (lane == 0) { red[2 * warp] = dot0; red[2 * warp + 1] = dot1; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s0 = 0, s1 = 0;
-            for (int i = 0; i < nwarp; ++i) { s0 += red[2 * i]; s1 += red[2 * i + 1]; }
-            double* pp = a.dot_part + (((size_t)s * 3 + c) * L.Nx + ix) * 4;
-            pp[0] = s0; pp[1] = s1; pp[2] = 0.0; pp[3] = 0.0;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// The same register-resident slab passes for My = Mz = 128: lane = q + 4p
-// holds the 16 elements p + 8r of its line.  A length-16 DFT over the
-// registers (4 x 4), the twiddles exp(-+2 pi i p k / 128), a transpose that
-// gives lane j the values of k = j and k = j + 8 from the 8 lanes of the line,
-// and two length-8 DFTs leave element j + 8m of the transform in register m
-// of lane j (m = 2 k2 + h for k = j + 8h + 16 k2): the same (lane, register)
-// <-> index map as the input.  Slab buffer rows of 68 (= 4 mod 16) values.
-// ---------------------------------------------------------------------------
-constexpr int R128_SLS = 68;
-
-struct Slab128Smem {
-    float2 tw[128];
-    float2 cf[EELS_MAX_MAT], dg[EELS_MAX_MAT];
-    float2 S[128 * R128_SLS];
-    float2 tile[FFT_THREADS / 32][R128_TILE];
-    int4 ci[64];                                 // this slab's column table (contiguous columns)
-};
-
-// HALF: Ny = Nz = 64 (the lattice fills exactly half of every line).
-template <bool HALF, bool FAST>
-__global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_fwd128(LatticeDev L, MatvecArgs<float> a) {
-    using C = float2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Slab128Smem& sm = *reinterpret_cast<Slab128Smem*>(smem_raw);
-    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
-    if (a.active && !a.active[s]) return;
-    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
-    const int nwarp = blockDim.x >> 5;
-    const float2* twg = tw_of<float>(L, 1);          // My = Mz = 128: the y and z tables coincide
-    for (int t = threadIdx.x; t < 128; t += blockDim.x) sm.tw[t] = twg[t];
-    if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
-    if (FAST)
-        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
-    const bool one_mat = L.nmat == 1;
-    __syncthreads();
-    float2* tile = sm.tile[warp];
-    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
-    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
-    const C zero = make_float2(0.f, 0.f);
-    // y transforms of the Nz columns, 4 per warp: gathered from x, into S
-    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
-        const int iz = iz0 + q;
-        C v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int y = p + 8 * r;
-            v[r] = zero;
-            if ((HALF ? r < 8 : y < Ny) && iz < Nz) {
-                const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
-                if (dip >= 0) v[r] = xs[dip] * (one_mat ? sm.cf[0] : sm.cf[L.mat[dip]]);
-            }
-        }
-        fft128_warp<false>(v, tile, q, p, sm.tw);
-        if (iz < Nz) {
-#pragma unroll
-            for (int m = 0; m < 16; ++m) sm.S[(p + 8 * m) * R128_SLS + iz] = v[m];
-        }
-    }
-    __syncthreads();
-    // z transforms of the 128 rows, 4 per warp: from S, written to U
-    C* U = a.U + (((size_t)s * 3 + c) * 128 * L.Nx + ix) * 128;
-    const size_t row = (size_t)L.Nx * 128;
-    for (int ky0 = warp * 4; ky0 < 128; ky0 += nwarp * 4) {
-        const int ky = ky0 + q;
-        C v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int z = p + 8 * r;
-            v[r] = (HALF ? r < 8 : z < Nz) ? sm.S[ky * R128_SLS + z] : zero;
-        }
-        fft128_warp<false>(v, tile, q, p, sm.tw);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) U[(size_t)ky * row + p + 8 * m] = v[m];
-    }
-}
-
-template <bool HALF, bool FAST>
-__global__ void __launch_bounds__(FFT_THREADS, 2) k_slab_inv128(LatticeDev L, MatvecArgs<float> a, float invM) {
-    using C = float2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Slab128Smem& sm = *reinterpret_cast<Slab128Smem*>(smem_raw);
-    __shared__ float red[2 * FFT_THREADS / 32];
-    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
-    if (a.active && !a.active[s]) return;
-    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
-    const int nwarp = blockDim.x >> 5;
-    const float2* twg = tw_of<float>(L, 2);
-    for (int t = threadIdx.x; t < 128; t += blockDim.x) sm.tw[t] = twg[t];
-    if (threadIdx.x < EELS_MAX_MAT) {
-        sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
-        sm.dg[threadIdx.x] = to_f(a.diag[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
-    }
-    if (FAST)
-        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
-    const bool one_mat = L.nmat == 1;
-    __syncthreads();
-    float2* tile = sm.tile[warp];
-    // inverse z transforms of the 128 rows of U, first Nz outputs into S
-    const C* U = a.U + (((size_t)s * 3 + c) * 128 * L.Nx + ix) * 128;
-    const size_t row = (size_t)L.Nx * 128;
-    for (int ky0 = warp * 4; ky0 < 128; ky0 += nwarp * 4) {
-        const int ky = ky0 + q;
-        C v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = U[(size_t)ky * row + p + 8 * r];
-        fft128_warp<true>(v, tile, q, p, sm.tw);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int z = p + 8 * m;
-            if (HALF ? m < 8 : z < Nz) sm.S[ky * R128_SLS + z] = v[m];
-        }
-    }
-    __syncthreads();
-    // inverse y transforms of the Nz columns, first Ny outputs combined with x and scattered
-    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
-    C* ys = a.y + ((size_t)s * 3 + c) * L.N;
-    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
-    float dot0 = 0.f, dot1 = 0.f;
-    for (int iz0 = warp * 4; iz0 < Nz; iz0 += nwarp * 4) {
-        const int iz = iz0 + q;
-        C v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = iz < Nz ? sm.S[(p + 8 * r) * R128_SLS + iz] : make_float2(0.f, 0.f);
-        fft128_warp<true>(v, tile, q, p, sm.tw);
-        if (iz >= Nz) continue;
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int y = p + 8 * m;
-            if (HALF ? m >= 8 : y >= Ny) continue;
-            const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
-            if (dip < 0) continue;
-            const int mt = one_mat ? 0 : L.mat[dip];
-            const C xv = xs[dip];
-            const C yv = sm.dg[mt] * xv - sm.cf[mt] * (invM * v[m]);
-            ys[dip] = yv;
-            dot0 += xv.x * yv.x - xv.y * yv.y;
-            dot1 += xv.x * yv.y + xv.y * yv.x;
-        }
-    }
-    if (a.dot_part) {
         for (int o = 16; o > 0; o >>= 1) {
             dot0 += __shfl_xor_sync(0xffffffffu, dot0, o);
             dot1 += __shfl_xor_sync(0xffffffffu, dot1, o);
@@ -1020,61 +896,37 @@ static void slab_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, 
     else k_slab_inv<Rl, CW><<<grid, FFT_THREADS, sm, st>>>(L, a, (Rl)(1.0 / ((double)L.Mx * L.My * L.Mz)));
 }
 
-// Register-resident slab kernels: FP32 with 64-point y and z transforms.
-template <typename Rl> static bool slab64_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st);
-template <> bool slab64_launch<double>(const LatticeDev&, const MatvecArgs<double>&, bool, cudaStream_t) { return false; }
-template <> bool slab64_launch<float>(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
-    if (L.My != 64 || L.Mz != 64) return false;
-    dim3 grid(L.Nx, a.S * 3);
-    count_launch();
+// Register-resident slab kernels: FP32 with 64- or 128-point y and z transforms.
+template <int R, bool HALF, bool FAST>
+static void slab_r_launch(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
+    const dim3 grid(L.Nx, a.S * 3);
+    const size_t sm = sizeof(SlabRSmem<R>);
     const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
-    const size_t sm = sizeof(Slab64Smem);
-    const bool half = L.Ny == 32 && L.Nz == 32;
-    if (half && L.contig) {
-        if (!inv) k_slab_fwd64<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv64<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    } else if (half) {
-        if (!inv) k_slab_fwd64<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv64<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    } else if (L.contig) {
-        if (!inv) k_slab_fwd64<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv64<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    } else {
-        if (!inv) k_slab_fwd64<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv64<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    }
-    return true;
+    if (!inv) k_slab_fwd_r<R, HALF, FAST><<<grid, FFT_THREADS, sm, st>>>(L, a);
+    else k_slab_inv_r<R, HALF, FAST><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
 }
 
-template <typename Rl> static bool slab128_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st);
-template <> bool slab128_launch<double>(const LatticeDev&, const MatvecArgs<double>&, bool, cudaStream_t) { return false; }
-template <> bool slab128_launch<float>(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
-    if (L.My != 128 || L.Mz != 128) return false;
-    dim3 grid(L.Nx, a.S * 3);
+template <int R>
+static void slab_r_any(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
+    const bool half = 2 * L.Ny == 8 * R && 2 * L.Nz == 8 * R;
     count_launch();
-    const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
-    const size_t sm = sizeof(Slab128Smem);
-    const bool half = L.Ny == 64 && L.Nz == 64;
-    if (half && L.contig) {
-        if (!inv) k_slab_fwd128<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv128<true, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    } else if (half) {
-        if (!inv) k_slab_fwd128<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv128<true, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    } else if (L.contig) {
-        if (!inv) k_slab_fwd128<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv128<false, true><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    } else {
-        if (!inv) k_slab_fwd128<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a);
-        else k_slab_inv128<false, false><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
-    }
-    return true;
+    if (half && L.contig) slab_r_launch<R, true, true>(L, a, inv, st);
+    else if (half) slab_r_launch<R, true, false>(L, a, inv, st);
+    else if (L.contig) slab_r_launch<R, false, true>(L, a, inv, st);
+    else slab_r_launch<R, false, false>(L, a, inv, st);
+}
+
+template <typename Rl> static bool slab_reg_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, cudaStream_t st);
+template <> bool slab_reg_launch<double>(const LatticeDev&, const MatvecArgs<double>&, bool, cudaStream_t) { return false; }
+template <> bool slab_reg_launch<float>(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
+    if (L.My == 64 && L.Mz == 64) { slab_r_any<8>(L, a, inv, st); return true; }
+    if (L.My == 128 && L.Mz == 128) { slab_r_any<16>(L, a, inv, st); return true; }
+    return false;
 }
 
 template <typename Rl> static void slab_launch_any(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, int cw,
                                                    cudaStream_t st) {
-    if (slab64_launch<Rl>(L, a, inv, st)) return;
-    if (slab128_launch<Rl>(L, a, inv, st)) return;
+    if (slab_reg_launch<Rl>(L, a, inv, st)) return;
     if (cw == 32) slab_launch<Rl, 32>(L, a, inv, st);
     else if (cw == 16) slab_launch<Rl, 16>(L, a, inv, st);
     else slab_launch<Rl, 8>(L, a, inv, st);
@@ -1176,22 +1028,22 @@ void prepare_far_kernels();
 void prepare_kernels() {
     prepare_w<float, 8>(); prepare_w<float, 16>(); prepare_w<float, 32>();
     prepare_w<double, 8>(); prepare_w<double, 16>(); prepare_w<double, 32>();
-    allow_smem(k_slab_fwd64<true, true>);
-    allow_smem(k_slab_fwd64<true, false>);
-    allow_smem(k_slab_fwd64<false, true>);
-    allow_smem(k_slab_fwd64<false, false>);
-    allow_smem(k_slab_inv64<true, true>);
-    allow_smem(k_slab_inv64<true, false>);
-    allow_smem(k_slab_inv64<false, true>);
-    allow_smem(k_slab_inv64<false, false>);
-    allow_smem(k_slab_fwd128<true, true>);
-    allow_smem(k_slab_fwd128<true, false>);
-    allow_smem(k_slab_fwd128<false, true>);
-    allow_smem(k_slab_fwd128<false, false>);
-    allow_smem(k_slab_inv128<true, true>);
-    allow_smem(k_slab_inv128<true, false>);
-    allow_smem(k_slab_inv128<false, true>);
-    allow_smem(k_slab_inv128<false, false>);
+    allow_smem(k_slab_fwd_r<8, true, true>);
+    allow_smem(k_slab_fwd_r<8, true, false>);
+    allow_smem(k_slab_fwd_r<8, false, true>);
+    allow_smem(k_slab_fwd_r<8, false, false>);
+    allow_smem(k_slab_inv_r<8, true, true>);
+    allow_smem(k_slab_inv_r<8, true, false>);
+    allow_smem(k_slab_inv_r<8, false, true>);
+    allow_smem(k_slab_inv_r<8, false, false>);
+    allow_smem(k_slab_fwd_r<16, true, true>);
+    allow_smem(k_slab_fwd_r<16, true, false>);
+    allow_smem(k_slab_fwd_r<16, false, true>);
+    allow_smem(k_slab_fwd_r<16, false, false>);
+    allow_smem(k_slab_inv_r<16, true, true>);
+    allow_smem(k_slab_inv_r<16, true, false>);
+    allow_smem(k_slab_inv_r<16, false, true>);
+    allow_smem(k_slab_inv_r<16, false, false>);
     prepare_far_kernels();
 }
 

@@ -282,9 +282,11 @@ __global__ void k_qmr_update(KrylovArgs<Rl> k, int n) {
 }
 
 
+// About four elements per thread and system: when only a few systems are
+// still iterating, their vector passes still spread over the whole GPU.
 static inline dim3 vec_grid(int n3, int S) {
     int bx = (n3 + 1023) / 1024;
-    if (bx > 64) bx = 64;
+    if (bx > 1024) bx = 1024;
     return dim3(bx, S);
 }
 

@@ -29,117 +29,222 @@
 
 namespace eels {
 
+// Bulk copies and their mbarrier (sm_90+ PTX).  Every wait is bounded: a
+// wait that gives up counts into g_wait_timeouts, which the host reads
+// after a solve (EELS_E_TIMEOUT).
+__device__ unsigned int g_wait_timeouts = 0;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The calling thread announces `bytes` of transfer on the barrier.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 1-D bulk copy global -> shared, completing on the barrier (16-byte aligned
+// addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits for phase `parity` of the barrier, at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, unsigned limit) {
+    const unsigned addr = smem_u32(bar);
+    for (unsigned i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 constexpr int XR_WARPS = 4;
 constexpr int XR_THREADS = 32 * XR_WARPS;
+constexpr unsigned XR_WAIT_POLLS = 1u << 22;
 
 template <int MX> struct XReg {
     static constexpr bool SPLIT = MX == 128;
     static constexpr int LPW = SPLIT ? 2 : 4;           // kz columns per warp
-    static constexpr int KZB = LPW * XR_WARPS;          // kz columns per block
+    static constexpr int ZT = LPW * XR_WARPS;           // kz' rows of D-hat per block
+    static constexpr int HX = MX / 2 + 1;
+    // shared row stride of the D-hat tile (8-byte words): the lanes of a load
+    // differ in row by (lane & 1) (Mx = 128) or (lane & 3) (Mx = 64) and in
+    // kx' by 2p + h or p, so a stride of 8 or 4 mod 16 puts the 16 lanes of
+    // each half-warp on distinct bank pairs
+    static constexpr int RS = SPLIT ? ((6 * HX + 7) / 16 * 16 + 8) : ((6 * HX + 11) / 16 * 16 + 4);
 };
+static_assert(XReg<128>::RS % 16 == 8 && XReg<128>::RS >= 6 * XReg<128>::HX, "row stride");
+static_assert(XReg<64>::RS % 16 == 4 && XReg<64>::RS >= 6 * XReg<64>::HX, "row stride");
 
+// One block per D-hat octant tile (ky' = blockIdx.y, kz' in [z0, z0 + ZT))
+// and group of systems (a.spb consecutive systems, blockIdx.z).  The tile
+// (and, in the first tile, the row kz' = Mz/2) comes into shared memory by
+// bulk copies and serves every (ky, kz) whose octant image lies in it: ky in
+// {ky', My - ky'} and kz in {kz', Mz - kz'} -- up to four passes over ZT kz
+// columns; the column kz' = 0, its own mirror, hands its mirror pass to
+// kz = Mz/2.  The systems of the group that share the tile's energy (the
+// beams of one energy) reuse it: it is copied again only when the system's
+// D-hat slot changes.  The last tile may be partial (Mz/2 not a multiple of
+// ZT): its columns past Mz/2 idle.
 template <int MX>
 __global__ void __launch_bounds__(XR_THREADS, 4) k_xpass_reg(LatticeDev L, MatvecArgs<float> a) {
     using X = XReg<MX>;
     constexpr bool SPLIT = X::SPLIT;
+    constexpr int ZT = X::ZT;
     __shared__ float2 tws[MX];                          // exp(-2 pi i t / MX)
+    __shared__ float2 tw2[7 * 8];                       // w64^(p k) at [k - 1][p]: lanes p read consecutive words
     __shared__ float2 tiles[XR_WARPS][R64_TILE];
-    const int s = blockIdx.z;
-    if (a.active && !a.active[s]) return;
-    const int ky = blockIdx.y;
+    __shared__ __align__(16) float2 dt[(ZT + 1) * X::RS];
+    __shared__ __align__(8) unsigned long long bar;
+    const int kyr = blockIdx.y, z0 = blockIdx.x * ZT;
+    const int Mz = L.Mz, Nx = L.Nx, My = L.My, Hx = L.Hx;
+    const int s_begin = blockIdx.z * a.spb, s_end = min(a.S, s_begin + a.spb);
+    const size_t row = (size_t)6 * Hx;                  // float2 per kz' row of D-hat (= 6 HX)
+    const int nrow = min(ZT, Mz / 2 - z0);              // rows of this tile
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    for (int t = threadIdx.x; t < MX; t += XR_THREADS) tws[t] = L.tw32x[t];
+    for (int t = threadIdx.x; t < 7 * 8; t += XR_THREADS) tw2[t] = L.tw32x[(MX / 64) * (t & 7) * ((t >> 3) + 1)];
+    __syncthreads();
+
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
     const int h = SPLIT ? (q >> 1) : 0;                 // frequency parity (Mx = 128)
-    const int kz = blockIdx.x * X::KZB + warp * X::LPW + (SPLIT ? (q & 1) : q);
-    const int Mz = L.Mz, Nx = L.Nx;
-    for (int t = threadIdx.x; t < MX; t += XR_THREADS) tws[t] = L.tw32x[t];
-    __syncthreads();
+    const int j = warp * X::LPW + (SPLIT ? (q & 1) : q);   // this lane's column of the tile
     float2* tile = tiles[warp];
-    auto tw = [&](int k) { return tws[(MX / 64) * p * k]; };   // w64^(p k)
-
+    auto tw = [&](int k) { return tw2[(k - 1) * 8 + p]; };   // w64^(p k)
     const size_t plane = (size_t)Nx * Mz;
-    const size_t cstride = (size_t)L.My * plane;
-    float2* U0 = a.U + ((size_t)s * 3 * L.My + ky) * plane + kz;
-    float2 v[3][8];
+    const size_t cstride = (size_t)My * plane;
     const float2 zero = make_float2(0.f, 0.f);
     constexpr int RIN = SPLIT ? 8 : 4;                  // registers that can hold lattice rows
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const int ix = p + 8 * r;
-            v[c][r] = (r < RIN && ix < Nx) ? U0[c * cstride + (size_t)ix * Mz] : zero;
-        }
-    if constexpr (SPLIT) {                              // odd frequencies: x_n w128^n
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const float2 w = h ? tws[p + 8 * r] : make_float2(1.f, 0.f);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * w;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) fft64_warp_t<false, !SPLIT>(v[c], tile, q, p, tw);
+    const int nky = (kyr == 0 || 2 * kyr == My) ? 1 : 2;
+    int cur_slot = -1;
+    unsigned phase = 0;
 
-    // D-hat product at kx = p + 8m (Mx = 64) or 2 (p + 8m) + h (Mx = 128); the
-    // octant index, and the sign sx of the odd components: -1 for m >= 4,
-    // where kx >= MX/2 (at kx = MX/2 those components vanish)
-    const int hy = L.My / 2, hz = Mz / 2;
-    const int kyr = ky <= hy ? ky : L.My - ky;
-    const int kzr = kz <= hz ? kz : Mz - kz;
-    const float sy = ky <= hy ? 1.f : -1.f, sz = kz <= hz ? 1.f : -1.f, syz = sy * sz;
-    const int Hx = L.Hx;
-    const float2* Dk = a.Dx + (((size_t)a.sys_slot[s] * L.Hy + kyr) * L.Hz + kzr) * 6 * Hx;
+    for (int s = s_begin; s < s_end; ++s) {
+        if (a.active && !a.active[s]) continue;
+        const int slot = a.sys_slot[s];
+        if (slot != cur_slot) {
+            // (re)fill the tile: every thread is done reading the previous one
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // one bulk copy per row (rows are 48 Hx bytes: 16-byte
+                // multiples) into rows of RS words
+                const float2* src = a.Dx + (((size_t)slot * L.Hy + kyr) * L.Hz + z0) * row;
+                const unsigned rb = (unsigned)(row * sizeof(float2));
+                mbar_expect_tx(&bar, rb * (nrow + (z0 == 0 ? 1 : 0)));
+                for (int r = 0; r < nrow; ++r) bulk_g2s(dt + r * X::RS, src + r * row, rb, &bar);
+                if (z0 == 0) bulk_g2s(dt + ZT * X::RS, src + (size_t)(Mz / 2) * row, rb, &bar);
+            }
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar, phase, XR_WAIT_POLLS))) {
+                // give up: record it, let the copies land before the block's
+                // shared memory is released, and leave
+                if (lane == 0) atomicAdd(&g_wait_timeouts, 1u);
+                mbar_wait(&bar, phase, XR_WAIT_POLLS);
+                return;
+            }
+            phase ^= 1u;
+            cur_slot = slot;
+        }
+        for (int pass = 0; pass < 2 * nky; ++pass) {
+            const int ky = (pass >> 1) ? My - kyr : kyr;
+            const bool mirror = pass & 1;
+            const bool nyq = mirror && z0 + j == 0;      // kz' = 0 hands its mirror pass to kz = Mz/2
+            const bool col_ok = z0 + j < Mz / 2;         // a column of a partial tile may idle
+            const int kz = !mirror ? z0 + j : (nyq ? Mz / 2 : Mz - (z0 + j));
+            const int drow = nyq ? ZT : j;
+            const float sy = (pass >> 1) ? -1.f : 1.f;
+            const float sz = (mirror && !nyq) ? -1.f : 1.f, syz = sy * sz;
+
+            float2* U0 = a.U + ((size_t)s * 3 * My + ky) * plane + (col_ok ? kz : 0);
+            float2 v[3][8];
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
-        const int kx = SPLIT ? 2 * (p + 8 * m) + h : p + 8 * m;
-        const int kxr = m < 4 ? kx : MX - kx;
-        const float sx = m < 4 ? 1.f : -1.f;
-        const float2* d = Dk + kxr;
-        const float2 dxx = __ldg(d);
-        const float2 dxy = (sx * sy) * __ldg(d + Hx);
-        const float2 dxz = (sx * sz) * __ldg(d + 2 * Hx);
-        const float2 dyy = __ldg(d + 3 * Hx);
-        const float2 dyz = syz * __ldg(d + 4 * Hx);
-        const float2 dzz = __ldg(d + 5 * Hx);
-        const float2 Xv = v[0][m], Yv = v[1][m], Zv = v[2][m];
-        v[0][m] = dxx * Xv + dxy * Yv + dxz * Zv;
-        v[1][m] = dxy * Xv + dyy * Yv + dyz * Zv;
-        v[2][m] = dxz * Xv + dyz * Yv + dzz * Zv;
-    }
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int ix = p + 8 * r;
+                    v[c][r] = (r < RIN && ix < Nx && col_ok) ? U0[c * cstride + (size_t)ix * Mz] : zero;
+                }
+            if constexpr (SPLIT) {                      // odd frequencies: x_n w128^n
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const float2 w = h ? tws[p + 8 * r] : make_float2(1.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * w;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) fft64_warp_t<false, !SPLIT>(v[c], tile, q, p, tw);
+
+            // D-hat product at kx = p + 8m (Mx = 64) or 2 (p + 8m) + h (Mx = 128):
+            // octant index kx', and the sign sx of the odd components (-1 for
+            // m >= 4, where kx >= MX/2; at kx = MX/2 those components vanish)
+            const float2* Dk = dt + (col_ok ? drow : 0) * X::RS;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int kx = SPLIT ? 2 * (p + 8 * m) + h : p + 8 * m;
+                const int kxr = m < 4 ? kx : MX - kx;
+                const float sx = m < 4 ? 1.f : -1.f;
+                const float2* d = Dk + kxr;
+                const float2 dxx = d[0];
+                const float2 dxy = (sx * sy) * d[Hx];
+                const float2 dxz = (sx * sz) * d[2 * Hx];
+                const float2 dyy = d[3 * Hx];
+                const float2 dyz = syz * d[4 * Hx];
+                const float2 dzz = d[5 * Hx];
+                const float2 Xv = v[0][m], Yv = v[1][m], Zv = v[2][m];
+                v[0][m] = dxx * Xv + dxy * Yv + dxz * Zv;
+                v[1][m] = dxy * Xv + dyy * Yv + dyz * Zv;
+                v[2][m] = dxz * Xv + dyz * Yv + dzz * Zv;
+            }
 
 #pragma unroll
-    for (int c = 0; c < 3; ++c) fft64_warp_t<true, false>(v[c], tile, q, p, tw);
-    if constexpr (SPLIT) {
-        // y_n = z0_n + w128^(-n) z1_n: the h = 1 lane twiddles its z1, lane
-        // h = 0 stores rows r < 4 and lane h = 1 rows r >= 4, each receiving
-        // the partner's half with one shuffle
+            for (int c = 0; c < 3; ++c) fft64_warp_t<true, false>(v[c], tile, q, p, tw);
+            if constexpr (SPLIT) {
+                // y_n = z0_n + w128^(-n) z1_n: the h = 1 lane twiddles its z1,
+                // lane h = 0 stores rows r < 4 and lane h = 1 rows r >= 4, each
+                // receiving the partner's half with one shuffle
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            float2 w = h ? tws[p + 8 * r] : make_float2(1.f, 0.f);
-            w.y = -w.y;
+                for (int r = 0; r < 8; ++r) {
+                    float2 w = h ? tws[p + 8 * r] : make_float2(1.f, 0.f);
+                    w.y = -w.y;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * w;
+                    for (int c = 0; c < 3; ++c) v[c][r] = v[c][r] * w;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const float2 send = h ? v[c][jj] : v[c][jj + 4];
+                        const float2 mine = h ? v[c][jj + 4] : v[c][jj];
+                        float2 got;
+                        got.x = __shfl_xor_sync(0xffffffffu, send.x, 2);
+                        got.y = __shfl_xor_sync(0xffffffffu, send.y, 2);
+                        const int ix = p + 8 * (jj + 4 * h);
+                        if (ix < Nx && col_ok) U0[c * cstride + (size_t)ix * Mz] = mine + got;
+                    }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int ix = p + 8 * r;
+                        if (ix < Nx && col_ok) U0[c * cstride + (size_t)ix * Mz] = v[c][r];
+                    }
+            }
         }
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 send = h ? v[c][j] : v[c][j + 4];
-                const float2 mine = h ? v[c][j + 4] : v[c][j];
-                float2 got;
-                got.x = __shfl_xor_sync(0xffffffffu, send.x, 2);
-                got.y = __shfl_xor_sync(0xffffffffu, send.y, 2);
-                const int ix = p + 8 * (j + 4 * h);
-                if (ix < Nx) U0[c * cstride + (size_t)ix * Mz] = mine + got;
-            }
-    } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int ix = p + 8 * r;
-                if (ix < Nx) U0[c * cstride + (size_t)ix * Mz] = v[c][r];
-            }
     }
 }
 
@@ -161,17 +266,33 @@ __global__ void k_dhat_interleave(LatticeDev L, int n_slot, const double2* __res
 }
 
 bool xpass_reg_supported(const LatticeDev& L) {
-    if (L.Mx == 64) return 2 * L.Nx <= 64 && L.Mz % XReg<64>::KZB == 0;
-    if (L.Mx == 128) return 2 * L.Nx <= 128 && L.Mz % XReg<128>::KZB == 0;
-    return false;
+    return (L.Mx == 64 || L.Mx == 128) && 2 * L.Nx <= L.Mx && L.Mz % 2 == 0;
 }
 
 bool launch_xpass_reg(const LatticeDev& L, const MatvecArgs<float>& a, cudaStream_t st) {
     if (!a.Dx || !xpass_reg_supported(L)) return false;
+    const int spb = a.spb > 0 ? a.spb : 1;
+    MatvecArgs<float> b = a;
+    b.spb = spb;
+    const unsigned groups = (unsigned)((a.S + spb - 1) / spb);
     count_launch();
-    if (L.Mx == 64) k_xpass_reg<64><<<dim3(L.Mz / XReg<64>::KZB, L.My, a.S), XR_THREADS, 0, st>>>(L, a);
-    else k_xpass_reg<128><<<dim3(L.Mz / XReg<128>::KZB, L.My, a.S), XR_THREADS, 0, st>>>(L, a);
+    if (L.Mx == 64) {
+        constexpr int ZT = XReg<64>::ZT;
+        k_xpass_reg<64><<<dim3((L.Mz / 2 + ZT - 1) / ZT, L.Hy, groups), XR_THREADS, 0, st>>>(L, b);
+    } else {
+        constexpr int ZT = XReg<128>::ZT;
+        k_xpass_reg<128><<<dim3((L.Mz / 2 + ZT - 1) / ZT, L.Hy, groups), XR_THREADS, 0, st>>>(L, b);
+    }
     return true;
+}
+
+unsigned int wait_timeouts() {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
 }
 
 void launch_dhat_interleave(const LatticeDev& L, int n_slot, const double2* Dr64, float2* Dx, cudaStream_t st) {

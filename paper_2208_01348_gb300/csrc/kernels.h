@@ -54,6 +54,8 @@ struct MatvecArgs {
                                   // three-pass path's last kernel
     const float2* Dx;             // FP32 D-hat [slot][Hy][Hz][6][Hx] (register x pass), or nullptr
     int S;
+    int spb;                      // systems per x-pass block (consecutive systems that usually share a
+                                  // D-hat slot: the beams of one energy); 0 or 1: one
 };
 
 // Returns true when a.dot_part was filled (three-pass path).
@@ -71,6 +73,9 @@ void launch_dhat_interleave(const LatticeDev& L, int n_slot, const double2* Dr64
 // the arguments do not suit it (the caller then launches the shared-memory one).
 bool xpass_reg_supported(const LatticeDev& L);
 bool launch_xpass_reg(const LatticeDev& L, const MatvecArgs<float>& a, cudaStream_t st);
+// Bounded device-side waits that gave up since the library was loaded (each
+// one left its kernel's results incomplete).  Reading it synchronises the device.
+unsigned int wait_timeouts();
 
 size_t matvec_smem_bytes(const LatticeDev& L, bool fp64);
 // Times the x pass with every tile width whose shared memory fits, on the

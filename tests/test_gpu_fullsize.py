@@ -93,6 +93,25 @@ def test_rod_map_full_size_block_of_beams_certified(dd):
         _certify(w, 31, ib, res, 0, beams=beams)
 
 
+def test_rod_map_full_size_block_of_32_beams(dd):
+    """One energy of the rod map with 32 raster beams in one batch (the FFT x
+    pass reuses each staged D-hat tile over 16 beams): six beams certified by
+    the oracle, and two of them bit-identical to solving them alone."""
+    w = I.config_rod_map(n_energy=64)
+    pick = np.arange(0, 1024, 32)                 # one beam per raster row
+    beams = w.beams_nm[pick]
+    ie = np.array([40])
+    res = _gpu(dd, w, ie, beams=beams)
+    assert res.converged.all()
+    for ib in (0, 5, 13, 21, 28, 31):
+        _certify(w, 40, ib, res, 0, beams=beams)
+    for ib in (0, 21):
+        solo = _gpu(dd, w, ie, beams=beams[ib:ib + 1])
+        assert solo.p_eels[0, 0] == res.p_eels[0, ib]
+        assert solo.p_cl[0, 0] == res.p_cl[0, ib]
+        assert np.array_equal(solo.p[0, 0], res.p[0, ib])
+
+
 def test_cherenkov_full_size_certified(dd):
     """64^3 silver sphere (137,376 dipoles, 128^3 FFT) in eps_h = 4 + 0.05i at
     200 keV (beta_h > 1)."""

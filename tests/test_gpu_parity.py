@@ -231,6 +231,39 @@ def test_reduced_rod_map_block_of_beams(dd, ctx):
             _check_point(res, ie, ib, _oracle(w, ie, ib, beams), 1e-10, 1e-10)
 
 
+def test_32_beams_of_one_energy_match_lu_and_solo_solves(dd, ctx):
+    """A spherical gold shell in a 17^3 box (padded 64 x 36 x 36: the mixed
+    path's FP32 rounds and the register x pass, which reuses one staged D-hat
+    tile over up to 16 beams): 32 beams of one energy in one batch against
+    the oracle's LU solve, and bit-identical to the beams solved alone."""
+    n = 17
+    c = (np.arange(n) + 0.5) - n / 2.0
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rr = np.sqrt(x * x + y * y + z * z)
+    occ = ((rr >= 6.5) & (rr <= 8.5)).astype(np.uint8)
+    d_nm, e_eV = 2.0, 2.4
+    dd.eels_set_grid(ctx, occ, d_nm)
+    assert dd.eels_padded_dims(ctx) == (64, 36, 36)
+    ang = np.linspace(0.0, 2.0 * np.pi, 32, endpoint=False)
+    beams = np.stack([24.0 * np.cos(ang), 24.0 * np.sin(ang)], axis=1)
+    o = dd.eels_default_opts(ekin_keV=100.0, precision=dd.EELS_MIXED, eps_it=1e-10)
+    eps_p, eps_h = [[I.drude(e_eV)]], [2.1025]
+    res = dd.eels_solve(ctx, o, [e_eV], eps_p, eps_h, beams, want_p=True)
+    assert res.converged.all()
+    pts = [run.setup(n, n, n, d_nm, occ, e_eV, eps_p[0], eps_h[0], beams[ib], ekin_keV=100.0) for ib in (0, 7, 16, 31)]
+    A = green.dense_matrix(pts[0].r, pts[0].k, pts[0].alpha)
+    for ib, pt in zip((0, 7, 16, 31), pts):
+        p_t = np.linalg.solve(A, pt.E_inc.reshape(-1)).reshape(-1, 3)
+        ref = run.observables(pt, p_t)
+        for key, got in (("P_EELS", res.p_eels), ("P_CL", res.p_cl), ("P_ext", res.p_ext), ("P_abs", res.p_abs)):
+            assert abs(got[0, ib] - ref[key]) <= 1e-4 * abs(ref[key]), (key, ib, got[0, ib], ref[key])
+        assert rel(res.p[0, ib], run.p_si(pt, p_t)) < 1e-4
+    for ib in (3, 16):
+        solo = dd.eels_solve(ctx, o, [e_eV], eps_p, eps_h, beams[ib:ib + 1], want_p=True)
+        assert solo.p_eels[0, 0] == res.p_eels[0, ib] and solo.p_cl[0, 0] == res.p_cl[0, ib]
+        assert np.array_equal(solo.p[0, 0], res.p[0, ib])
+
+
 def test_batch_composition_does_not_change_results(dd, ctx):
     """A point solved alone and inside a larger batch gives identical bits."""
     w = I.reduced(I.config_spectrum(), 10 / 32, n_energy=4)
@@ -556,3 +589,61 @@ def test_solve_dev_is_bit_identical_to_host_solve(dd, ctx):
     with pytest.raises(dd.EelsError) as e:
         dd.eels_solve_dev(ctx, o, et.cpu(), ept, eht, bt, out["eels"])
     assert e.value.code == dd.EELS_E_INVALID_ARG
+
+
+# ------------------------------------------------------------------ several materials, extrapolation
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_three_material_particle_solve_matches_lu(dd, ctx, prec):
+    """A 12^3 sphere of three concentric materials (Drude gold core, a
+    dielectric shell, Drude silver outside) in glass: every probability and
+    p against the oracle's LU solve."""
+    n, diam = 12, 24.0
+    c = ((np.arange(n) + 0.5) - n / 2.0) * (diam / n)
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    rr = np.sqrt(x * x + y * y + z * z)
+    occ = np.where(rr <= 5.0, 1, np.where(rr <= 8.0, 2, np.where(rr <= diam / 2, 3, 0))).astype(np.uint8)
+    assert set(np.unique(occ)) == {0, 1, 2, 3}
+    e_eV = 2.6
+    eps_p = [I.drude(e_eV), 2.25 + 0.1j, I.drude(e_eV, I.DRUDE_AG)]
+    eps_h, beam = 2.1025, (18.0, 3.0)
+    dd.eels_set_grid(ctx, occ, diam / n)
+    o = dd.eels_default_opts(ekin_keV=120.0, precision=getattr(dd, "EELS_" + prec), eps_it=1e-12 if prec == "FP64" else 1e-9)
+    res = dd.eels_solve(ctx, o, [e_eV], [eps_p], [eps_h], [beam], want_p=True)
+    ref = run.solve_point(n, n, n, diam / n, occ, e_eV, eps_p, eps_h, beam, ekin_keV=120.0)
+    tol = 1e-10 if prec == "FP64" else 1e-4
+    for key, got in (("P_EELS", res.p_eels), ("P_CL", res.p_cl), ("P_ext", res.p_ext), ("P_abs", res.p_abs)):
+        assert abs(got[0, 0] - ref[key]) <= tol * abs(ref[key]), (key, got[0, 0], ref[key])
+    assert rel(res.p[0, 0], ref["p"]) < tol
+
+
+def test_library_extrapolation_to_zero_dipole_size_matches_oracle_and_mie(dd, ctx):
+    """Sec. 3.2 through the library: a 20 nm absorbing dielectric sphere in
+    vacuum on nine volume-corrected lattices (10^3 to 32^3 cells), each solved
+    on the GPU (FP64) and by the oracle, extrapolated to d = 0 with
+    eels_extrapolate: per-lattice and extrapolated values agree with the
+    oracle's, and the extrapolated P_EELS and P_CL lie within their 95 %
+    intervals of the Lorenz-Mie solution."""
+    from oracle import mie_eels, physics
+    from oracle.extrapolate import extrapolate_to_zero
+    ek, diam, b, e_eV, eps_p, eps_h = 100.0, 20.0, 25.0, 2.5, 2.25 + 0.5j, 1.0
+    coef = mie_eels.electron_coefficients(eps_h, e_eV, b * NM, physics.electron_speed(ek), 16, 17.5 * NM)
+    exact = mie_eels.eels_cl_from(coef, diam / 2 * NM, eps_p, eps_h)
+    ds, gpu, ora = [], [], []
+    o = dd.eels_default_opts(ekin_keV=ek, precision=dd.EELS_FP64, eps_it=1e-11)
+    for n in (10, 12, 14, 16, 18, 20, 24, 28, 32):
+        occ = I.sphere_occupancy(n, diam)
+        d = (np.pi * diam ** 3 / 6 / int(occ.sum())) ** (1 / 3)
+        dd.eels_set_grid(ctx, occ, d)
+        r = dd.eels_solve(ctx, o, [e_eV], [[eps_p]], [eps_h], [(b, 0.0)])
+        ref = run.solve_point(n, n, n, d, occ, e_eV, [eps_p], eps_h, (b, 0.0), ekin_keV=ek, method="fft", rtol=1e-11)
+        ds.append(d)
+        gpu.append((r.p_eels[0, 0], r.p_cl[0, 0]))
+        ora.append((ref["P_EELS"], ref["P_CL"]))
+    for j in (0, 1):
+        g = np.array([v[j] for v in gpu])
+        y = np.array([v[j] for v in ora])
+        assert np.max(np.abs(g - y) / np.abs(y)) < 1e-8
+        v0, ci = dd.eels_extrapolate(ds, g)
+        r0, rci = extrapolate_to_zero(np.array(ds), y)
+        assert abs(v0 - r0) <= 1e-7 * abs(r0) and abs(ci - rci) <= 1e-5 * rci
+        assert abs(v0 - exact[j]) <= ci, (j, v0 / exact[j] - 1, ci / exact[j])
