@@ -18,6 +18,7 @@ Module map (each function cites the paper passage it follows):
   physics    -- electron speed, host index, beta_h/gamma_h (Eq. 24), polarizability
   field      -- incident field (Eq. 25) and auxiliary field (Eq. 34)
   green      -- Green's tensor (Eq. 5), dense DDA matrix, FFT matvec
+  igt        -- cell-integrated Green's tensor and polarizability to second order in kd (Sec. S5)
   losses     -- P_EELS (Eq. 32, 37), P_ext (Eq. 17, 48), P_abs (Eq. 18), P_CL (Eq. 42)
   icosphere  -- far-field direction grid
   mie        -- plane-wave Lorenz-Mie cross sections (a pin for the DDA core)

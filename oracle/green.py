@@ -73,7 +73,7 @@ class FFTOperator:
     reproduces the dense sum exactly (G~ is set to 0 at zero separation and
     at the unused wrap index n)."""
 
-    def __init__(self, idx, n_axes, d, k, alpha, workers=-1):
+    def __init__(self, idx, n_axes, d, k, alpha, workers=-1, interaction="point"):
         self.idx = np.asarray(idx)
         self.n = tuple(int(v) for v in n_axes)
         self.m = tuple(2 * v for v in self.n)
@@ -94,7 +94,12 @@ class FFTOperator:
             sl[ax] = nv
             valid[tuple(sl)] = False
         G = np.zeros(self.m + (3, 3), dtype=np.complex128)
-        G[valid] = green_tilde(R[valid], k)
+        if interaction == "igt_so":
+            from . import igt
+            offsets = np.rint(R[valid] / d).astype(int)
+            G[valid] = igt.green_lattice(offsets, k, d)
+        else:
+            G[valid] = green_tilde(R[valid], k)
         self.D = np.stack([sfft.fftn(G[..., a, b], workers=workers) for a, b in PAIRS])
 
     def conv(self, x):

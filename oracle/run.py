@@ -47,9 +47,14 @@ class Point:
     eps_h: complex
     n_axes: tuple
     d: float
+    interaction: str = "point"     # "point" (Eq. 5 at the cell centres) or "igt_so" (oracle/igt.py)
 
 
-def setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None, v=None, direction=None):
+def setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None, v=None, direction=None,
+          interaction="point", polarizability="cm"):
+    """interaction / polarizability: "point" / "cm" (point dipoles, Clausius-
+    Mossotti with radiative reaction) or "igt_so" / "igt_so" (the cell-
+    integrated Green's tensor to second order in kd, Sec. S5; oracle/igt.py)."""
     if v is None:
         v = physics.electron_speed(ekin_keV)
     omega = float(physics.omega_of(energy_eV))
@@ -60,25 +65,36 @@ def setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None
     d = d_nm * NM
     m2 = np.asarray(eps_p, dtype=np.complex128)[mat - 1] / complex(eps_h)   # m = m_p / m_h (Eq. 2)
     a_cm = physics.polarizability_cm(m2, d)
-    a = physics.polarizability_rr(a_cm, k)
+    if polarizability == "igt_so":
+        from . import igt
+        a = igt.polarizability_igt_so(a_cm, k, d)
+    else:
+        a = physics.polarizability_rr(a_cm, k)
     x0, y0 = beam_nm[0] * NM, beam_nm[1] * NM
     if direction is None:
         E = field.incident_field(r, omega, v, m_h, gamma, x0, y0)
         Ea = field.auxiliary_field(r, omega, v, m_h, gamma, x0, y0)
     else:
         E, Ea = field.fields_along(r, omega, v, m_h, gamma, x0, y0, direction)
-    return Point(omega, k, m_h, beta, gamma, v, idx, r, a, a_cm, E, Ea, complex(eps_h), (nx, ny, nz), d)
+    return Point(omega, k, m_h, beta, gamma, v, idx, r, a, a_cm, E, Ea, complex(eps_h), (nx, ny, nz), d, interaction)
+
+
+def system_matrix(pt: Point):
+    """The dense 3N x 3N matrix of the point's interaction model."""
+    if pt.interaction == "igt_so":
+        from . import igt
+        return igt.dense_matrix_so(pt.idx, pt.k, pt.alpha, pt.d)
+    return green.dense_matrix(pt.r, pt.k, pt.alpha)
 
 
 def solve_lu(pt: Point):
-    A = green.dense_matrix(pt.r, pt.k, pt.alpha)
-    return np.linalg.solve(A, pt.E_inc.reshape(-1)).reshape(-1, 3)
+    return np.linalg.solve(system_matrix(pt), pt.E_inc.reshape(-1)).reshape(-1, 3)
 
 
 def solve_fft(pt: Point, rtol=1e-12, restart=200, maxiter=20000, workers=-1, x0=None):
     """Library GMRES on the lattice FFT operator, Jacobi-scaled:
     (alpha^1/2 A alpha^1/2) y = alpha^1/2 E, p = alpha^1/2 y."""
-    op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha, workers=workers)
+    op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha, workers=workers, interaction=pt.interaction)
     sq = np.sqrt(pt.alpha)
     n3 = 3 * len(pt.r)
 
@@ -98,7 +114,7 @@ def solve_fft(pt: Point, rtol=1e-12, restart=200, maxiter=20000, workers=-1, x0=
 def residual(pt: Point, p, op: Optional[green.FFTOperator] = None):
     """||E_inc - A p|| / ||E_inc|| with the oracle's own FFT operator."""
     if op is None:
-        op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha)
+        op = green.FFTOperator(pt.idx, pt.n_axes, pt.d, pt.k, pt.alpha, interaction=pt.interaction)
     r = pt.E_inc - op.matvec(p)
     return float(np.linalg.norm(r) / np.linalg.norm(pt.E_inc))
 
@@ -132,8 +148,10 @@ def p_si(pt: Point, p_t):
 
 
 def solve_point(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=None, v=None,
-                method="lu", want_cl=True, want_img=False, rtol=1e-12, direction=None):
-    pt = setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=ekin_keV, v=v, direction=direction)
+                method="lu", want_cl=True, want_img=False, rtol=1e-12, direction=None, interaction="point",
+                polarizability="cm"):
+    pt = setup(nx, ny, nz, d_nm, occ, energy_eV, eps_p, eps_h, beam_nm, ekin_keV=ekin_keV, v=v, direction=direction,
+               interaction=interaction, polarizability=polarizability)
     if method == "lu":
         p_t = solve_lu(pt)
     else:
