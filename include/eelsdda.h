@@ -67,6 +67,21 @@ enum { EELS_FP64 = 0, EELS_MIXED = 1 };          /* precision of the Krylov iter
  * three-term Lanczos recurrence (both for complex-symmetric matrices),
  * EELS_BICGSTAB = BiCGStab with the conjugated inner product. */
 enum { EELS_QMR = 0, EELS_BICGSTAB = 1, EELS_QMR2 = 2 };
+/* Interaction term and polarizability (the options the paper recommends,
+ * Sec. S5, "-int igt_so" and "-pol igt_so"; it gives no formulas, this
+ * library's reading):
+ *   EELS_INT_POINT  the Green's tensor (Eq. 5) between cell centres;
+ *   EELS_INT_IGT_SO the Green's tensor averaged over the source cell, with
+ *                   exp(ik|R - s|) expanded around the cell centre to second
+ *                   order in k and the geometric cell integrals exact, for
+ *                   lattice offsets of max-norm <= 3 (the point tensor beyond);
+ *   EELS_POL_CM     Clausius-Mossotti with radiative reaction,
+ *                   1/alpha = 1/alpha_CM - (2/3) i k^3;
+ *   EELS_POL_IGT_SO also the k^2 term of the cell's own field:
+ *                   1/alpha = 1/alpha_CM - (2/3)(c1 k^2 d^2 + i k^3 d^3)/d^3,
+ *                   c1 = 3 ln(2 + sqrt 3) - pi/2. */
+enum { EELS_INT_POINT = 0, EELS_INT_IGT_SO = 1 };
+enum { EELS_POL_CM = 0, EELS_POL_IGT_SO = 1 };
 
 typedef struct { double re, im; } eels_c128;
 
@@ -97,6 +112,8 @@ typedef struct {
                                 takes z to n (a half turn about x for n = -z); the phase of Eq. 25 is
                                 referred to that point.  The paper's electron moves along z (Sec. 2.2;
                                 the direction option of its solver, Sec. S5) */
+    int interaction;         /* EELS_INT_POINT (default) or EELS_INT_IGT_SO */
+    int polarizability;      /* EELS_POL_CM (default) or EELS_POL_IGT_SO */
 } eels_opts;
 
 typedef struct {
@@ -107,7 +124,8 @@ typedef struct {
 } eels_point_stats;
 
 /* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR2, eps_it 1e-8,
- * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 1000
+ * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 1000,
+ * beam along +z, EELS_INT_POINT, EELS_POL_CM
  * (FP32 Lanczos recurrences lose biorthogonality on hard systems; restarting
  * every 1000 iterations from the FP64 residual keeps the iteration count
  * near that of the FP64 solve). */
@@ -229,6 +247,12 @@ int eels_incident_field_dir(eels_ctx* ctx, double ekin_keV, double energy_eV, ee
  * FP32 FFT path (the same kernels eels_solve uses).  eps_p [n_mat]. */
 int eels_apply_matrix(eels_ctx* ctx, int precision, double energy_eV, int n_mat, const eels_c128* eps_p,
                       eels_c128 eps_h, int n_vec, const eels_c128* x, eels_c128* y);
+
+/* Interaction term and polarizability used by eels_apply_matrix and
+ * eels_prepare_operator of this context (eels_solve takes them from its
+ * eels_opts); default EELS_INT_POINT, EELS_POL_CM.  EELS_E_INVALID_ARG for
+ * unknown values. */
+int eels_set_interaction(eels_ctx* ctx, int interaction, int polarizability);
 
 /* Prepare the Jacobi-scaled operator A' = I - a^1/2 G~' a^1/2 (lattice
  * units: lengths in d, a = alpha~/d^3) for one system per entry, so that

@@ -243,7 +243,8 @@ struct eels_ctx {
     DevBuf kv[7];                                          // Krylov vectors V0 V1 P0 P1 P2 W X
     DevBuf part_a, part_b, qmr, bicg, active, upd, counters, outer, res, rnorm, eps_sys;
     DevBuf sysf, coef, diag, wabs, wdv, slot, kappa_sys;
-    DevBuf G, Dr64, Dr32, Dx32, kappa_slot;
+    DevBuf G, Dr64, Dr32, Dx32, kappa_slot, igt_tab;
+    int interaction = EELS_INT_POINT, polarizability = EELS_POL_CM;   // eels_set_interaction
     DevBuf lpart, lsums, fpart, fsums, dirs, wts;
     int dirs_n = 0;
     int* pinned = nullptr;
@@ -261,7 +262,7 @@ struct eels_ctx {
     std::vector<DevBuf*> buffers() {
         std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &colinfo, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
                                   &part_a, &part_b, &qmr, &bicg, &active, &upd, &counters, &outer, &res, &rnorm, &eps_sys,
-                                  &sysf, &coef, &diag, &wabs, &wdv, &slot, &kappa_sys, &G, &Dr64, &Dr32, &Dx32, &kappa_slot,
+                                  &sysf, &coef, &diag, &wabs, &wdv, &slot, &kappa_sys, &G, &Dr64, &Dr32, &Dx32, &kappa_slot, &igt_tab,
                                   &lpart, &lsums, &fpart, &fsums, &dirs, &wts};
         for (auto& b : kv) v.push_back(&b);
         for (auto& b : tw64) v.push_back(&b);
@@ -399,7 +400,10 @@ double electron_speed(double ekin_keV) {
     return kC * std::sqrt(1.0 - 1.0 / (g * g));
 }
 
-EnergyPar energy_params(double ekin, double e_eV, cd eps_h, int n_mat, const eels_c128* eps_p, double d_m) {
+// pol: EELS_POL_CM (Clausius-Mossotti with radiative reaction) or
+// EELS_POL_IGT_SO (the cell's self term to second order in kd, igt.cu).
+EnergyPar energy_params(double ekin, double e_eV, cd eps_h, int n_mat, const eels_c128* eps_p, double d_m,
+                        int pol = EELS_POL_CM) {
     if (!(e_eV > 0)) throw Fail{EELS_E_INVALID_ARG, "energies must be positive"};
     if (eps_h.imag() < 0) throw Fail{EELS_E_INVALID_ARG, "Im eps_h < 0: active host medium (excluded, Sec. 2.1)"};
     EnergyPar p{};
@@ -422,7 +426,11 @@ EnergyPar energy_params(double ekin, double e_eV, cd eps_h, int n_mat, const eel
     for (int m = 0; m < n_mat; ++m) {
         const cd m2 = cz(eps_p[m]) / eps_h;                                     // m^2 = eps_p / eps_h
         const cd acm = 3.0 / (4.0 * kPi) * (m2 - 1.0) / (m2 + 2.0);           // alpha'_CM = alpha~_CM / d^3
-        const cd al = acm / (1.0 - cd(0.0, 2.0 / 3.0) * k3 * acm);            // radiative reaction
+        // 1/alpha' = 1/alpha'_CM - (2/3) i kappa^3 (radiative reaction), and
+        // with igt_so also - (2/3) c1 kappa^2 (the k^2 term of the cell's self field)
+        cd self = cd(0.0, 2.0 / 3.0) * k3;
+        if (pol == EELS_POL_IGT_SO) self += (2.0 / 3.0) * IGT_C1 * p.kappa * p.kappa;
+        const cd al = acm / (1.0 - self * acm);
         p.alpha[m] = al;
         p.sa[m] = std::sqrt(al);
         p.alpha_inv[m] = 1.0 / al;
@@ -550,6 +558,18 @@ size_t per_system_bytes(const LatticeDev& L, bool fp64) {
 
 size_t per_slot_bytes(const LatticeDev& L) {
     return (size_t)6 * L.Hx * L.Hy * L.Hz * (sizeof(double2) + 2 * sizeof(float2));
+}
+
+// The lattice description for a D-hat build with the given interaction term
+// (uploads the igt_so cell tables on first use).
+LatticeDev dhat_lattice(eels_ctx* c, int interaction) {
+    LatticeDev L = c->L;
+    L.igt = nullptr;
+    if (interaction == EELS_INT_IGT_SO) {
+        if (!c->igt_tab.p) h2d(c->igt_tab, igt_tables(), c->stream);
+        L.igt = c->igt_tab.as<double>();
+    }
+    return L;
 }
 
 // Iterations allowed per inner solve: an FP32 inner solve may be restarted
@@ -894,6 +914,10 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         throw Fail{EELS_E_INVALID_ARG, "unknown solver"};
     if (!(o->eps_it > 0) || o->max_iter <= 0) throw Fail{EELS_E_INVALID_ARG, "eps_it and max_iter must be positive"};
     if (p_cl && o->n_dir <= 0) throw Fail{EELS_E_INVALID_ARG, "p_cl requested with n_dir = 0"};
+    if (o->interaction != EELS_INT_POINT && o->interaction != EELS_INT_IGT_SO)
+        throw Fail{EELS_E_INVALID_ARG, "unknown interaction term"};
+    if (o->polarizability != EELS_POL_CM && o->polarizability != EELS_POL_IGT_SO)
+        throw Fail{EELS_E_INVALID_ARG, "unknown polarizability"};
     const BeamFrame frame = beam_frame(o->beam_dir);
     if (frame.along_z) check_beams(c, n_beam, beams);
     else check_beams_dir(c, n_beam, beams, frame);
@@ -903,7 +927,8 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
     const double d_m = c->d_nm * 1e-9;
     std::vector<EnergyPar> ep(n_energy);
     for (int e = 0; e < n_energy; ++e)
-        ep[e] = energy_params(o->ekin_keV, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m);
+        ep[e] = energy_params(o->ekin_keV, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m,
+                              o->polarizability);
     const bool fp64 = o->precision == EELS_FP64;
     const unsigned timeouts0 = wait_timeouts();
     // far-field directions
@@ -968,7 +993,8 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         for (int q0 = 0; q0 < n_slot; q0 += gchunk) {
             const int nq = std::min(gchunk, n_slot - q0);
             const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
-            launch_dhat_build(L, nq, c->kappa_slot.as<double2>() + q0, c->G.as<double2>(), c->Dr64.as<double2>() + q0 * hs,
+            launch_dhat_build(dhat_lattice(c, o->interaction), nq, c->kappa_slot.as<double2>() + q0, c->G.as<double2>(),
+                              c->Dr64.as<double2>() + q0 * hs,
                               c->Dr32.as<float2>() + q0 * hs, st, c->Dx32.as<float2>() + q0 * hs);
         }
         CK(cudaGetLastError());
@@ -1136,6 +1162,21 @@ void eels_default_opts(eels_opts* o) {
     o->beam_dir[0] = 0.0;
     o->beam_dir[1] = 0.0;
     o->beam_dir[2] = 1.0;
+    o->interaction = EELS_INT_POINT;
+    o->polarizability = EELS_POL_CM;
+}
+
+int eels_set_interaction(eels_ctx* c, int interaction, int polarizability) {
+    if (!c) return EELS_E_INVALID_ARG;
+    return guarded(c, [&] {
+        if (interaction != EELS_INT_POINT && interaction != EELS_INT_IGT_SO)
+            throw Fail{EELS_E_INVALID_ARG, "unknown interaction term"};
+        if (polarizability != EELS_POL_CM && polarizability != EELS_POL_IGT_SO)
+            throw Fail{EELS_E_INVALID_ARG, "unknown polarizability"};
+        c->interaction = interaction;
+        c->polarizability = polarizability;
+        return EELS_OK;
+    });
 }
 
 int eels_create(eels_ctx** out, int device, void* cuda_stream) {
@@ -1301,7 +1342,7 @@ int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, c
         cudaStream_t st = c->stream;
         const LatticeDev& L = c->L;
         const double d_m = c->d_nm * 1e-9;
-        EnergyPar p = energy_params(100.0, energy_eV, cz(eps_h), n_mat, eps_p, d_m);
+        EnergyPar p = energy_params(100.0, energy_eV, cz(eps_h), n_mat, eps_p, d_m, c->polarizability);
         const int S = n_vec, n3 = 3 * c->N;
         const size_t hs = (size_t)6 * L.Hx * L.Hy * L.Hz;
         c->Dr64.ensure(hs * sizeof(double2));
@@ -1310,7 +1351,8 @@ int eels_apply_matrix(eels_ctx* c, int precision, double energy_eV, int n_mat, c
         c->G.ensure((size_t)6 * L.Mx * L.My * L.Mz * sizeof(double2));
         std::vector<double2> ks(1, d2(p.kappa));
         h2d(c->kappa_slot, ks, st);
-        launch_dhat_build(L, 1, c->kappa_slot.as<double2>(), c->G.as<double2>(), c->Dr64.as<double2>(), c->Dr32.as<float2>(), st,
+        launch_dhat_build(dhat_lattice(c, c->interaction), 1, c->kappa_slot.as<double2>(), c->G.as<double2>(),
+                          c->Dr64.as<double2>(), c->Dr32.as<float2>(), st,
                           c->Dx32.as<float2>());
         std::vector<double2> coef((size_t)S * EELS_MAX_MAT, make_double2(1, 0)), diag((size_t)S * EELS_MAX_MAT);
         for (int s = 0; s < S; ++s)
@@ -1382,7 +1424,8 @@ int eels_prepare_operator(eels_ctx* c, int n_energy, const double* energy_eV, in
         // D-hat slot (the beams of one energy)
         int run = 0, max_run = 1;
         for (int e = 0; e < S; ++e) {
-            EnergyPar p = energy_params(100.0, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m);
+            EnergyPar p = energy_params(100.0, energy_eV[e], cz(eps_h[e]), n_mat, eps_p + (size_t)e * n_mat, d_m,
+                                        c->polarizability);
             const bool same = e > 0 && energy_eV[e] == energy_eV[e - 1] && eps_h[e].re == eps_h[e - 1].re &&
                               eps_h[e].im == eps_h[e - 1].im &&
                               std::memcmp(eps_p + (size_t)e * n_mat, eps_p + (size_t)(e - 1) * n_mat,
@@ -1395,7 +1438,8 @@ int eels_prepare_operator(eels_ctx* c, int n_energy, const double* energy_eV, in
         }
         h2d(c->kappa_slot, kap, st);
         for (size_t e = 0; e < kap.size(); ++e)
-            launch_dhat_build(L, 1, c->kappa_slot.as<double2>() + e, c->G.as<double2>(), c->Dr64.as<double2>() + e * hs,
+            launch_dhat_build(dhat_lattice(c, c->interaction), 1, c->kappa_slot.as<double2>() + e, c->G.as<double2>(),
+                              c->Dr64.as<double2>() + e * hs,
                               c->Dr32.as<float2>() + e * hs, st, c->Dx32.as<float2>() + e * hs);
         c->spb = std::min(max_run, 16);
         h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->slot, slot, st);

@@ -397,7 +397,25 @@ __global__ void k_green(LatticeDev L, const double2* kappa, double2* G) {
     double2 g[6];
     for (int c = 0; c < 6; ++c) g[c] = make_double2(0.0, 0.0);
     const double rn2 = rx * rx + ry * ry + rz * rz;
-    if (ok && rn2 > 0.0) {
+    const bool near = L.igt && fabs(rx) <= IGT_NEAR && fabs(ry) <= IGT_NEAR && fabs(rz) <= IGT_NEAR;
+    if (ok && rn2 > 0.0 && near) {
+        // cell-averaged tensor to second order in kappa: exp(i kappa R)(-T0 + i kappa T1 + kappa^2 T2)
+        const int side = 2 * IGT_NEAR + 1;
+        const double* t = L.igt + ((size_t)(((int)rz + IGT_NEAR) * side + ((int)ry + IGT_NEAR)) * side +
+                                   ((int)rx + IGT_NEAR)) * 18;
+        const double rn = sqrt(rn2);
+        const double2 kap = kappa[slot];
+        double sn, cs;
+        sincos(kap.x * rn, &sn, &cs);
+        const double ex = exp(-kap.y * rn);
+        const double2 ph = make_double2(ex * cs, ex * sn);
+        const double2 ik = make_double2(-kap.y, kap.x);
+        const double2 k2 = kap * kap;
+        for (int c = 0; c < 6; ++c) {
+            const double2 v = make_double2(-t[c], 0.0) + t[6 + c] * ik + t[12 + c] * k2;
+            g[c] = ph * v;
+        }
+    } else if (ok && rn2 > 0.0) {
         const double rn = sqrt(rn2);
         const double h[3] = {rx / rn, ry / rn, rz / rn};
         const double2 kap = kappa[slot];

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <vector>
 
 #include "common.cuh"
 #include "fft.cuh"
@@ -31,6 +32,8 @@ struct LatticeDev {
     const int4* colinfo;          // [Nx][Ny] (index of the column's first dipole - first, first, last+1, 0)
     int contig;                   // 1 if every column's occupied cells are contiguous in z (colinfo is exact)
     int nmat;                     // materials used by the lattice (1: one coefficient per system)
+    const double* igt;            // D-hat build only: cell tables of the igt_so interaction (igt.cu), or
+                                  // nullptr for point dipoles
     FftPlan px, py, pz;
     int xw32, xw64;               // x-pass tile width chosen by the autotuner (0: size heuristic)
     const double2* tw64x; const double2* tw64y; const double2* tw64z;   // exp(-2 pi i t / M)
@@ -57,6 +60,14 @@ struct MatvecArgs {
     int spb;                      // systems per x-pass block (consecutive systems that usually share a
                                   // D-hat slot: the beams of one energy); 0 or 1: one
 };
+
+// Cell-integrated Green's tensor (igt_so): lattice offsets of max-norm <=
+// IGT_NEAR take exp(i kappa R) (-T0 + i kappa T1 + kappa^2 T2); the host
+// table holds, per offset (x fastest over [-IGT_NEAR, IGT_NEAR]^3), T0, T1,
+// T2 in the component order xx xy xz yy yz zz (18 doubles), lattice units.
+constexpr int IGT_NEAR = 3;
+constexpr double IGT_C1 = 2.3800773639795505;   // integral of 1/|u| over the unit cube: 3 ln(2 + sqrt 3) - pi/2
+const std::vector<double>& igt_tables();
 
 // Returns true when a.dot_part was filled (three-pass path).
 template <typename Rl>

@@ -35,6 +35,10 @@ EELS_MIXED = 1
 EELS_QMR = 0
 EELS_BICGSTAB = 1
 EELS_QMR2 = 2
+EELS_INT_POINT = 0
+EELS_INT_IGT_SO = 1
+EELS_POL_CM = 0
+EELS_POL_IGT_SO = 1
 
 
 class eels_c128(C.Structure):
@@ -54,7 +58,7 @@ class eels_opts(C.Structure):
     _fields_ = [("ekin_keV", C.c_double), ("precision", C.c_int), ("solver", C.c_int),
                 ("eps_it", C.c_double), ("eps_inner", C.c_double), ("max_iter", C.c_int),
                 ("n_dir", C.c_int), ("max_batch", C.c_int), ("inner_max_iter", C.c_int),
-                ("beam_dir", C.c_double * 3)]
+                ("beam_dir", C.c_double * 3), ("interaction", C.c_int), ("polarizability", C.c_int)]
 
 
 class eels_point_stats(C.Structure):
@@ -103,6 +107,7 @@ _sig = {
     "eels_apply_matrix": (C.c_int, [_P, C.c_int, C.c_double, C.c_int, _cp, eels_c128, C.c_int, _cp, _cp]),
     "eels_directions": (C.c_int, [C.c_int, _dp, _dp]),
     "eels_prepare_operator": (C.c_int, [_P, C.c_int, _dp, C.c_int, _cp, _cp]),
+    "eels_set_interaction": (C.c_int, [_P, C.c_int, C.c_int]),
     "eels_matvec_dev": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_kernel_launches": (C.c_longlong, []),
     "eels_cl_total": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
@@ -338,6 +343,11 @@ def eels_apply_matrix(ctx, precision: int, energy_eV: float, eps_p, eps_h: compl
     _check(_lib.eels_apply_matrix(ctx, precision, energy_eV, len(ep), _cptr(ep), eels_c128(eh.real, eh.imag),
                                   x.shape[0], _cptr(x), _cptr(y)), ctx)
     return y[0] if single else y
+
+
+def eels_set_interaction(ctx, interaction: int = EELS_INT_POINT, polarizability: int = EELS_POL_CM) -> None:
+    """Interaction term and polarizability of eels_apply_matrix / eels_prepare_operator."""
+    _check(_lib.eels_set_interaction(ctx, int(interaction), int(polarizability)), ctx)
 
 
 def eels_prepare_operator(ctx, energies_eV, eps_p, eps_h) -> None:

@@ -647,3 +647,53 @@ def test_library_extrapolation_to_zero_dipole_size_matches_oracle_and_mie(dd, ct
         r0, rci = extrapolate_to_zero(np.array(ds), y)
         assert abs(v0 - r0) <= 1e-7 * abs(r0) and abs(ci - rci) <= 1e-5 * rci
         assert abs(v0 - exact[j]) <= ci, (j, v0 / exact[j] - 1, ci / exact[j])
+
+
+# ------------------------------------------------------------------ igt_so (Sec. S5)
+@pytest.mark.parametrize("dims", [(5, 4, 6), (7, 3, 9), (32, 3, 8), (13, 6, 17)])
+def test_igt_so_matvec_equals_dense_oracle(dd, ctx, dims):
+    """The cell-integrated interaction and polarizability (igt_so) through
+    eels_apply_matrix, FP64 and FP32, against the oracle's dense matrix."""
+    nx, ny, nz = dims
+    occ = _random_grid(dims, seed=nx + 3 * ny + 7 * nz, nmat=2)
+    d_nm, e_eV = 2.0, 2.3
+    eps_p, eps_h = [I.drude(e_eV), 3.0 + 0.4j], 2.0 + 0.1j
+    dd.eels_set_grid(ctx, occ, d_nm)
+    dd.eels_set_interaction(ctx, dd.EELS_INT_IGT_SO, dd.EELS_POL_IGT_SO)
+    try:
+        pt = run.setup(nx, ny, nz, d_nm, occ, e_eV, eps_p, eps_h, (100.0, 100.0), ekin_keV=100.0,
+                       interaction="igt_so", polarizability="igt_so")
+        A = run.system_matrix(pt)
+        x = I.random_complex((2, len(pt.r), 3), seed=9)
+        ref = np.stack([(A @ xi.reshape(-1)).reshape(-1, 3) for xi in x])
+        y64 = dd.eels_apply_matrix(ctx, dd.EELS_FP64, e_eV, eps_p, eps_h, x)
+        y32 = dd.eels_apply_matrix(ctx, dd.EELS_MIXED, e_eV, eps_p, eps_h, x)
+    finally:
+        dd.eels_set_interaction(ctx, dd.EELS_INT_POINT, dd.EELS_POL_CM)
+    for i in range(2):
+        assert rel(y64[i], ref[i]) < 1e-12
+        assert rel(y32[i], ref[i]) < 2e-5
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_igt_so_solve_matches_lu(dd, ctx, prec):
+    """A 12^3 high-index sphere (eps = 15 + i) in glass with the igt_so
+    interaction and polarizability: probabilities and p against the oracle's
+    LU solve of the same model."""
+    w = I.config_small_sphere()
+    g = w.grid
+    e_eV, eps_p, eps_h, beam = 2.5, 15.0 + 1.0j, 2.1025, (16.0, 2.0)
+    dd.eels_set_grid(ctx, g.occ, g.d_nm)
+    o = dd.eels_default_opts(ekin_keV=120.0, precision=getattr(dd, "EELS_" + prec),
+                             eps_it=1e-12 if prec == "FP64" else 1e-9,
+                             interaction=dd.EELS_INT_IGT_SO, polarizability=dd.EELS_POL_IGT_SO)
+    res = dd.eels_solve(ctx, o, [e_eV], [[eps_p]], [eps_h], [beam], want_p=True)
+    ref = run.solve_point(g.nx, g.ny, g.nz, g.d_nm, g.occ, e_eV, [eps_p], eps_h, beam, ekin_keV=120.0,
+                          interaction="igt_so", polarizability="igt_so")
+    pnt = run.solve_point(g.nx, g.ny, g.nz, g.d_nm, g.occ, e_eV, [eps_p], eps_h, beam, ekin_keV=120.0)
+    tol = 1e-10 if prec == "FP64" else 1e-4
+    for key, got in (("P_EELS", res.p_eels), ("P_CL", res.p_cl), ("P_ext", res.p_ext), ("P_abs", res.p_abs)):
+        assert abs(got[0, 0] - ref[key]) <= tol * abs(ref[key]), (key, got[0, 0], ref[key])
+    assert rel(res.p[0, 0], ref["p"]) < tol
+    # the model differs from point dipoles by far more than the tolerance
+    assert abs(pnt["P_EELS"] / ref["P_EELS"] - 1.0) > 1e-3
