@@ -534,6 +534,7 @@ def main():
     # roofline of the FFT matvec (the dominant kernel set) on one batch's systems
     S = len(batches[0]) * n_beam
     tiles = dd.eels_tile_widths(ctx)
+    xtuned = dd.eels_tuned_xpass(ctx)
     ie0 = batches[0]
     dd.eels_prepare_operator(ctx, np.repeat(w.energies_eV[ie0], n_beam), np.repeat(w.eps_p[ie0], n_beam, axis=0),
                              np.repeat(w.eps_h[ie0], n_beam))
@@ -597,7 +598,9 @@ def main():
         "data": "synthetic (Drude permittivities stand in for tabulated optical data)",
         "config": {"workload": w.name, "points_per_gpu": n_e * n_beam, "points_per_step": E * n_beam,
                    "step": f"{E} energies x {n_beam} beams, batches cycled", "dipoles": n, "fft": [mx, my, mz],
-                   "precision": args.precision, "solver": args.solver, "x_tile": list(tiles), "eps_it": 1e-8,
+                   "precision": args.precision, "solver": args.solver, "x_tile": list(tiles),
+                   "x_pass": {"mode": ["heuristic", "loads", "tensor copies"][xtuned[0]], "beams_per_block": xtuned[1]},
+                   "eps_it": 1e-8,
                    "eps_inner": 1e-5, "n_dir": w.n_dir,
                    "l2": "working set of a step > L2 (several GB of per-system vectors and FFT scratch)",
                    "iters_mean": float(np.mean(iters)), "residual_max": float(np.max(resid))},

@@ -160,6 +160,15 @@ int eels_padded_dims(const eels_ctx* ctx, int* mx, int* my, int* mz);
  * run (a size heuristic is used meanwhile). */
 int eels_tile_widths(const eels_ctx* ctx, int* xw32, int* xw64);
 
+/* Choices the library timed for the register x pass of the current grid
+ * (FFT x lengths 64 and 128, FP32) on the first eels_solve after
+ * eels_set_grid (no counterpart in the paper: a tuning step of this
+ * implementation): *mode 1 = U lines loaded and stored by the threads,
+ * 2 = moved by tensor copies (TMA) through shared memory; *spb = beams of
+ * one energy one block takes (its staged D-hat serves all of them).  0 and
+ * 0 until that solve has run, or when the grid does not use that pass. */
+int eels_tuned_xpass(const eels_ctx* ctx, int* mode, int* spb);
+
 /*
  * Solve every (energy, beam) point and reduce the losses.  Host buffers.
  *   energy_eV [n_energy]; eps_p [n_energy][n_mat] (relative permittivity of

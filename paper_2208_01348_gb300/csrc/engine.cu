@@ -256,8 +256,9 @@ struct eels_ctx {
     // operator prepared by eels_prepare_operator
     int op_systems = 0;
     // consecutive systems that share a D-hat slot (the beams of one energy):
-    // the x pass reuses a staged D-hat tile over up to this many of them
-    int spb = 1;
+    // the x pass reuses a staged D-hat tile over up to this many of them;
+    // spb_tuned is the autotuner's choice for the lattice (0: not tuned yet)
+    int spb = 1, spb_tuned = 0;
 
     std::vector<DevBuf*> buffers() {
         std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &colinfo, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
@@ -392,6 +393,8 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     c->has_grid = true;
     c->tuned = false;
     c->L.xw32 = c->L.xw64 = 0;
+    c->L.xmode = 0;
+    c->spb_tuned = 0;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
 }
 
@@ -957,7 +960,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
     }
     S_max = std::min(S_max, 21000);
     const int n_sys = n_energy * n_beam;
-    c->spb = std::max(1, std::min(n_beam, 16));
+    c->spb = std::max(1, std::min(n_beam, c->spb_tuned > 0 ? c->spb_tuned : 16));
     std::vector<int> iters(n_sys, 0), refin(n_sys, 0);
     std::vector<double> resid(n_sys, 0.0);
     bool all_conv = true;
@@ -1034,7 +1037,18 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
             // first solve on this lattice: time the x-pass tile widths on this
             // batch (the x pass only scrambles the FFT scratch), before any
             // inner-loop graph is captured; FP64 on a few systems only
-            // (the register-resident FP32 x pass has one shape: 16 kz lines per block)
+            // (the register-resident FP32 x pass: how U moves and how many beams
+            // of an energy a block takes are timed instead of the tile width)
+            if (xpass_reg_supported(L)) {
+                CK(cudaMemsetAsync(c->U.p, 0, (size_t)S * 3 * L.My * L.Nx * L.Mz * sizeof(float2), st));
+                int mode = 0, spb = 1;
+                autotune_xreg(L, mv_args<float>(c, S, c->u32.as<float2>(), c->kv[5].as<float2>(), c->Dr32.as<float2>(),
+                                                 nullptr, true),
+                              c->spb, st, &mode, &spb);
+                c->L.xmode = mode;
+                c->spb_tuned = spb;
+                c->spb = std::min(c->spb, spb);
+            }
             c->L.xw32 = xpass_reg_supported(L) ? 16
                                                : autotune_xpass<float>(L, mv_args<float>(c, S, c->u32.as<float2>(),
                                                                                           c->kv[5].as<float2>(),
@@ -1243,6 +1257,14 @@ int eels_tile_widths(const eels_ctx* c, int* xw32, int* xw64) {
     if (!c->has_grid) return EELS_E_NO_GRID;
     *xw32 = c->L.xw32;
     *xw64 = c->L.xw64;
+    return EELS_OK;
+}
+
+int eels_tuned_xpass(const eels_ctx* c, int* mode, int* spb) {
+    if (!c || !mode || !spb) return EELS_E_INVALID_ARG;
+    if (!c->has_grid) return EELS_E_NO_GRID;
+    *mode = c->L.xmode;
+    *spb = c->spb_tuned;
     return EELS_OK;
 }
 

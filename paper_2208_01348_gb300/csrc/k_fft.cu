@@ -1042,6 +1042,7 @@ template <typename Rl, int W> static void prepare_w() {
 }
 
 void prepare_far_kernels();
+void prepare_xreg_kernels();
 
 void prepare_kernels() {
     prepare_w<float, 8>(); prepare_w<float, 16>(); prepare_w<float, 32>();
@@ -1063,6 +1064,7 @@ void prepare_kernels() {
     allow_smem(k_slab_inv_r<16, false, true>);
     allow_smem(k_slab_inv_r<16, false, false>);
     prepare_far_kernels();
+    prepare_xreg_kernels();
 }
 
 template bool launch_matvec<float>(const LatticeDev&, const MatvecArgs<float>&, cudaStream_t);

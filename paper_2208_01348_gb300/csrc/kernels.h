@@ -36,6 +36,7 @@ struct LatticeDev {
                                   // nullptr for point dipoles
     FftPlan px, py, pz;
     int xw32, xw64;               // x-pass tile width chosen by the autotuner (0: size heuristic)
+    int xmode;                    // register x pass: 0 choose by availability, 1 direct loads, 2 tensor copies
     const double2* tw64x; const double2* tw64y; const double2* tw64z;   // exp(-2 pi i t / M)
     const float2* tw32x; const float2* tw32y; const float2* tw32z;
 };
@@ -84,6 +85,13 @@ void launch_dhat_interleave(const LatticeDev& L, int n_slot, const double2* Dr64
 // the arguments do not suit it (the caller then launches the shared-memory one).
 bool xpass_reg_supported(const LatticeDev& L);
 bool launch_xpass_reg(const LatticeDev& L, const MatvecArgs<float>& a, cudaStream_t st);
+// Times the register x pass on the systems of a (CUDA events on st; not
+// during a stream capture) for each way of moving U (direct loads, tensor
+// copies when available) and each number of systems per block in
+// {1, 2, 4, 8, 16} up to max_spb, and returns the fastest in *mode, *spb.
+// The x pass transforms a.U in place: its contents are lost.
+void autotune_xreg(const LatticeDev& L, const MatvecArgs<float>& a, int max_spb, cudaStream_t st, int* mode, int* spb);
+
 // Bounded device-side waits that gave up since the library was loaded (each
 // one left its kernel's results incomplete).  Reading it synchronises the device.
 unsigned int wait_timeouts();

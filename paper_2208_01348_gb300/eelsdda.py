@@ -115,6 +115,7 @@ _sig = {
     "eels_extrapolate": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp]),
     "eels_vacuum_equivalent": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(eels_vacuum_map)]),
     "eels_tile_widths": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "eels_tuned_xpass": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_krylov_solve_dev": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_double, C.c_int,
                                         C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
@@ -451,6 +452,13 @@ def eels_tile_widths(ctx):
     """(FP32, FP64) x-pass tile widths timed on the first solve of the grid (0: not yet)."""
     a, b = C.c_int(), C.c_int()
     _check(_lib.eels_tile_widths(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def eels_tuned_xpass(ctx):
+    """(mode, beams per block) timed for the register x pass (0, 0: not yet / not used)."""
+    a, b = C.c_int(), C.c_int()
+    _check(_lib.eels_tuned_xpass(ctx, C.byref(a), C.byref(b)), ctx)
     return a.value, b.value
 
 

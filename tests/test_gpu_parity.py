@@ -372,19 +372,28 @@ def test_mixed_fp32_rounds_match_oracle_above_fp64_threshold(dd, ctx, solver):
             assert abs(got[ie, 0] - ref[key]) <= 1e-4 * abs(ref[key]), (key, got[ie, 0], ref[key])
 
 
-def test_tile_autotuning_keeps_matvec_bits(dd, ctx):
-    """The first solve on a grid times the x-pass tile widths; matvecs before
-    and after the choice are bit-identical (the width only groups lines)."""
-    occ = _random_grid((13, 9, 11), seed=21, nmat=2)
+@pytest.mark.parametrize("dims", [(13, 9, 11), (20, 9, 16), (40, 6, 8)])
+def test_tile_autotuning_keeps_matvec_bits(dd, ctx, dims):
+    """The first solve on a grid times the x-pass tile widths (and, for x
+    lengths 64 and 128, how U moves and how many systems a block takes);
+    matvecs before and after the choice are bit-identical (the choices only
+    regroup the same arithmetic)."""
+    occ = _random_grid(dims, seed=21, nmat=2)
     dd.eels_set_grid(ctx, occ, 1.7)
     assert dd.eels_tile_widths(ctx) == (0, 0)
+    assert dd.eels_tuned_xpass(ctx) == (0, 0)
     eps_p, eps_h = [I.drude(2.2), 2.0 + 0.5j], 1.9 + 0j
     x = I.random_complex((2, dd.eels_num_dipoles(ctx), 3), seed=8)
     y_before = [dd.eels_apply_matrix(ctx, pr, 2.2, eps_p, eps_h, x) for pr in (dd.EELS_FP64, dd.EELS_MIXED)]
     o = dd.eels_default_opts(ekin_keV=100.0, eps_it=1e-6)
-    dd.eels_solve(ctx, o, [2.2, 2.9], [eps_p, eps_p], [eps_h, eps_h], [[20.0, 0.0]])
+    dd.eels_solve(ctx, o, [2.2, 2.9], [eps_p, eps_p], [eps_h, eps_h], [[50.0, 0.0]])
     w32, w64 = dd.eels_tile_widths(ctx)
     assert w32 in (8, 16, 32) and w64 in (8, 16, 32)
+    mode, spb = dd.eels_tuned_xpass(ctx)
+    if dd.eels_padded_dims(ctx)[0] in (64, 128):
+        assert mode in (1, 2) and spb == 1
+    else:
+        assert (mode, spb) == (0, 0)
     y_after = [dd.eels_apply_matrix(ctx, pr, 2.2, eps_p, eps_h, x) for pr in (dd.EELS_FP64, dd.EELS_MIXED)]
     for a, b in zip(y_before, y_after):
         assert np.array_equal(a, b)
