@@ -55,8 +55,8 @@ STEP_ENERGIES = {"cherenkov": 25, "spectrum": 200, "small": 1, "rod": 1}
 # parts, see oracle_point()), with the GMRES matvecs the oracle needs for
 # that point (bench.py --oracle-iterations prints them).
 CPU_SAMPLE = {"spectrum": (100, 0, None), "small": (0, 0, None),
-              "cherenkov": (50, 0, dict(iters=6, cl_stride=32, matvecs=1937)),
-              "rod": (4, 0, dict(iters=6, cl_stride=8, matvecs=None))}
+              "cherenkov": (50, 0, dict(iters=30, cl_stride=8, matvecs=1937)),
+              "rod": (4, 0, dict(iters=30, cl_stride=8, matvecs=897))}
 
 # ncu DRAM traffic (read + write bytes) of one matvec launch set, per system,
 # measured on the workload TRAFFIC_WORKLOAD with kernel sources that hash to
