@@ -641,6 +641,12 @@ template <int R> struct SlabRSmem {
     int4 ci[SlabR<R>::L / 2];                    // this slab's column table (contiguous columns)
 };
 
+// Persistent forward slab pass: the grid holds as many blocks as fit on the
+// GPU at once, and each block walks the (system, component, slab) items with
+// a stride of the grid size.  For single-material lattices with contiguous
+// columns, a block loads the first column quad of its next item while it runs
+// the z transforms of the current one, so the gather's latency is hidden
+// behind arithmetic instead of opening every item.
 template <int R, bool HALF, bool FAST>
 __global__ void __launch_bounds__(FFT_THREADS, R == 8 ? 4 : 2) k_slab_fwd_r(LatticeDev L, MatvecArgs<float> a) {
     using C = float2;
@@ -648,65 +654,104 @@ __global__ void __launch_bounds__(FFT_THREADS, R == 8 ? 4 : 2) k_slab_fwd_r(Latt
     constexpr int LEN = P::L, SLS = P::SLS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SlabRSmem<R>& sm = *reinterpret_cast<SlabRSmem<R>*>(smem_raw);
-    const int ix = blockIdx.x, b = blockIdx.y, s = b / 3, c = b % 3;
-    if (a.active && !a.active[s]) return;
-    const int Ny = L.Ny, Nz = L.Nz, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3, p = lane >> 2;
+    const int Ny = L.Ny, Nz = L.Nz, Nx = L.Nx, warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = lane & 3,
+              p = lane >> 2;
     const int nwarp = blockDim.x >> 5;
+    const int n_items = a.S * 3 * Nx;
+    const bool one_mat = L.nmat == 1;
+    const bool prefetch = FAST && one_mat;
     const float2* twg = tw_of<float>(L, 1);          // My = Mz: the y and z tables coincide
     for (int t = threadIdx.x; t < (R - 1) * 8; t += blockDim.x) sm.tw2[t] = twg[(t & 7) * ((t >> 3) + 1)];
-    if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
-    if (FAST)
-        for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
-    const bool one_mat = L.nmat == 1;
-    __syncthreads();
     float2* tile = sm.tile[warp];
     auto tw = [&](int k) { return sm.tw2[(k - 1) * 8 + p]; };
-    const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
-    const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
     const C zero = make_float2(0.f, 0.f);
     const int stride = nwarp * 4;
-    // y transforms of the Nz columns, 4 per warp: gathered from x, into S
-    auto gather = [&](int iz0, C (&v)[R]) {
-        const int iz = iz0 + q;
+    auto active = [&](int item) { return !a.active || a.active[item / (3 * Nx)]; };
+    auto next_item = [&](int item) {
+        for (item += gridDim.x; item < n_items && !active(item); item += gridDim.x) {}
+        return item;
+    };
+    // raw x values of the first column quad (iz0 = 4 warp) of an item, dipoles
+    // addressed through the column table in global memory
+    auto gather_raw = [&](int item, C (&v)[R]) {
+        const int s = item / (3 * Nx), c = (item / Nx) % 3, ix = item % Nx, iz = warp * 4 + q;
+        const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int y = p + 8 * r;
             v[r] = zero;
             if ((HALF ? r < R / 2 : y < Ny) && iz < Nz) {
-                const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
-                if (dip >= 0) v[r] = xs[dip] * (one_mat ? sm.cf[0] : sm.cf[L.mat[dip]]);
+                const int dip = col_dip(L.colinfo[(size_t)ix * Ny + y], iz);
+                if (dip >= 0) v[r] = xs[dip];
             }
         }
     };
-    C vn[R];
-    if (warp * 4 < Nz) gather(warp * 4, vn);
-    for (int iz0 = warp * 4; iz0 < Nz; iz0 += stride) {
-        C v[R];
+    C pf[R];
+    int item = blockIdx.x;
+    if (item < n_items && !active(item)) item = next_item(item);
+    if (prefetch && item < n_items && warp * 4 < Nz) gather_raw(item, pf);
+    for (; item < n_items;) {
+        const int s = item / (3 * Nx), c = (item / Nx) % 3, ix = item % Nx;
+        if (threadIdx.x < EELS_MAX_MAT) sm.cf[threadIdx.x] = to_f(a.coef[(size_t)s * EELS_MAX_MAT + threadIdx.x]);
+        if (FAST)
+            for (int t = threadIdx.x; t < Ny; t += blockDim.x) sm.ci[t] = L.colinfo[(size_t)ix * Ny + t];
+        __syncthreads();
+        const C* xs = a.x + ((size_t)s * 3 + c) * L.N;
+        const int* cm = L.cellmap + (size_t)ix * Ny * Nz;
+        // y transforms of the Nz columns, 4 per warp: gathered from x, into S
+        auto gather = [&](int iz0, C (&v)[R]) {
+            const int iz = iz0 + q;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = vn[r];
-        if (iz0 + stride < Nz) gather(iz0 + stride, vn);
-        fft_warp_t<R, false, HALF>(v, tile, q, p, tw);
-        const int iz = iz0 + q;
-        if (iz < Nz) {
+            for (int r = 0; r < R; ++r) {
+                const int y = p + 8 * r;
+                v[r] = zero;
+                if ((HALF ? r < R / 2 : y < Ny) && iz < Nz) {
+                    const int dip = FAST ? col_dip(sm.ci[y], iz) : cm[y * Nz + iz];
+                    if (dip >= 0) v[r] = xs[dip] * (one_mat ? sm.cf[0] : sm.cf[L.mat[dip]]);
+                }
+            }
+        };
+        C vn[R];
+        if (warp * 4 < Nz) {
+            if (prefetch) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) sm.S[(p + 8 * m) * SLS + iz] = v[m];
+                for (int r = 0; r < R; ++r) vn[r] = pf[r] * sm.cf[0];
+            } else {
+                gather(warp * 4, vn);
+            }
         }
-    }
-    __syncthreads();
-    // z transforms of the LEN rows, 4 per warp: from S, written to U
-    C* U = a.U + (((size_t)s * 3 + c) * LEN * L.Nx + ix) * LEN;
-    const size_t row = (size_t)L.Nx * LEN;
-    for (int ky0 = warp * 4; ky0 < LEN; ky0 += stride) {
-        const int ky = ky0 + q;
-        C v[R];
+        for (int iz0 = warp * 4; iz0 < Nz; iz0 += stride) {
+            C v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int z = p + 8 * r;
-            v[r] = (HALF ? r < R / 2 : z < Nz) ? sm.S[ky * SLS + z] : zero;
+            for (int r = 0; r < R; ++r) v[r] = vn[r];
+            if (iz0 + stride < Nz) gather(iz0 + stride, vn);
+            fft_warp_t<R, false, HALF>(v, tile, q, p, tw);
+            const int iz = iz0 + q;
+            if (iz < Nz) {
+#pragma unroll
+                for (int m = 0; m < R; ++m) sm.S[(p + 8 * m) * SLS + iz] = v[m];
+            }
         }
-        fft_warp_t<R, false, HALF>(v, tile, q, p, tw);
+        __syncthreads();
+        const int nxt = next_item(item);
+        if (prefetch && nxt < n_items && warp * 4 < Nz) gather_raw(nxt, pf);
+        // z transforms of the LEN rows, 4 per warp: from S, written to U
+        C* U = a.U + (((size_t)s * 3 + c) * LEN * L.Nx + ix) * LEN;
+        const size_t row = (size_t)L.Nx * LEN;
+        for (int ky0 = warp * 4; ky0 < LEN; ky0 += stride) {
+            const int ky = ky0 + q;
+            C v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) U[(size_t)ky * row + p + 8 * m] = v[m];
+            for (int r = 0; r < R; ++r) {
+                const int z = p + 8 * r;
+                v[r] = (HALF ? r < R / 2 : z < Nz) ? sm.S[ky * SLS + z] : zero;
+            }
+            fft_warp_t<R, false, HALF>(v, tile, q, p, tw);
+#pragma unroll
+            for (int m = 0; m < R; ++m) U[(size_t)ky * row + p + 8 * m] = v[m];
+        }
+        item = nxt;
+        __syncthreads();                              // S, ci and cf are refilled for the next item
     }
 }
 
@@ -915,13 +960,34 @@ static void slab_launch(const LatticeDev& L, const MatvecArgs<Rl>& a, bool inv, 
 }
 
 // Register-resident slab kernels: FP32 with 64- or 128-point y and z transforms.
+// Multiprocessors of the current device (queried once per device).
+static int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 132; }
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 132;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 template <int R, bool HALF, bool FAST>
 static void slab_r_launch(const LatticeDev& L, const MatvecArgs<float>& a, bool inv, cudaStream_t st) {
-    const dim3 grid(L.Nx, a.S * 3);
     const size_t sm = sizeof(SlabRSmem<R>);
     const float invM = (float)(1.0 / ((double)L.Mx * L.My * L.Mz));
-    if (!inv) k_slab_fwd_r<R, HALF, FAST><<<grid, FFT_THREADS, sm, st>>>(L, a);
-    else k_slab_inv_r<R, HALF, FAST><<<grid, FFT_THREADS, sm, st>>>(L, a, invM);
+    if (!inv) {
+        // persistent: the blocks resident at once (2 or 4 per multiprocessor)
+        const int items = a.S * 3 * L.Nx;
+        const int blocks = std::min(items, sm_count() * (R == 8 ? 4 : 2));
+        k_slab_fwd_r<R, HALF, FAST><<<blocks, FFT_THREADS, sm, st>>>(L, a);
+    } else {
+        k_slab_inv_r<R, HALF, FAST><<<dim3(L.Nx, a.S * 3), FFT_THREADS, sm, st>>>(L, a, invM);
+    }
 }
 
 template <int R>
