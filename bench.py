@@ -62,8 +62,8 @@ CPU_SAMPLE = {"spectrum": (100, 0, None), "small": (0, 0, None),
 # measured on the workload TRAFFIC_WORKLOAD with kernel sources that hash to
 # TRAFFIC_SRC_HASH; reported as null for other workloads (other FFT sizes,
 # other kernels) and when the kernel sources differ from the measured ones.
-TRAFFIC_BYTES_PER_SYSTEM = None
-TRAFFIC_SRC_HASH = ""
+TRAFFIC_BYTES_PER_SYSTEM = 115_781_008   # 1,852,496,128 B over 16 systems, 128^3 FFT
+TRAFFIC_SRC_HASH = "363b1e37f9ac0e7b"
 TRAFFIC_WORKLOAD = "cherenkov"
 
 
@@ -424,7 +424,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-sample", type=int, default=5,
                     help="energies of the plain FP64 single-system comparison (0: skip)")
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=0,
+                    help="steps of the end-to-end pass (default: one pass over the batches, at most 4)")
     ap.add_argument("--matvec-reps", type=int, default=20)
     args = ap.parse_args()
     if args.workload == "serve":
@@ -518,7 +519,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     pts_e2e, h2d, d2h = 0, 0, 0
-    for k in range(args.e2e_steps):
+    e2e_steps = args.e2e_steps if args.e2e_steps > 0 else min(len(batches), 4)
+    for k in range(e2e_steps):
         dd.eels_set_grid(ctx, g.occ, g.d_nm)
         ie, r2 = step(k)
         pts_e2e += len(ie) * n_beam
@@ -535,6 +537,9 @@ def main():
     S = len(batches[0]) * n_beam
     tiles = dd.eels_tile_widths(ctx)
     xtuned = dd.eels_tuned_xpass(ctx)
+    # every x-pass candidate the autotuner timed (ms of three launches)
+    xnames = ["heuristic", "loads", "tensor copies"]
+    xtimed = {f"{xnames[m]}, {b} beams/block": round(t, 4) for m, b, t in dd.eels_xpass_timings(ctx)}
     ie0 = batches[0]
     dd.eels_prepare_operator(ctx, np.repeat(w.energies_eV[ie0], n_beam), np.repeat(w.eps_p[ie0], n_beam, axis=0),
                              np.repeat(w.eps_h[ie0], n_beam))
@@ -599,13 +604,13 @@ def main():
         "config": {"workload": w.name, "points_per_gpu": n_e * n_beam, "points_per_step": E * n_beam,
                    "step": f"{E} energies x {n_beam} beams, batches cycled", "dipoles": n, "fft": [mx, my, mz],
                    "precision": args.precision, "solver": args.solver, "x_tile": list(tiles),
-                   "x_pass": {"mode": ["heuristic", "loads", "tensor copies"][xtuned[0]], "beams_per_block": xtuned[1]},
+                   "x_pass": {"mode": xnames[xtuned[0]], "beams_per_block": xtuned[1], "timed_ms": xtimed},
                    "eps_it": 1e-8,
                    "eps_inner": 1e-5, "n_dir": w.n_dir,
                    "l2": "working set of a step > L2 (several GB of per-system vectors and FFT scratch)",
                    "iters_mean": float(np.mean(iters)), "residual_max": float(np.max(resid))},
-        "e2e": {"value": pts_e2e * world / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d / args.e2e_steps),
-                "d2h_bytes_per_step": int(d2h / args.e2e_steps), "ms_per_step": e2e_s * 1e3 / args.e2e_steps},
+        "e2e": {"value": pts_e2e * world / e2e_s, "unit": "points/s", "h2d_bytes_per_step": int(h2d / e2e_steps),
+                "d2h_bytes_per_step": int(d2h / e2e_steps), "ms_per_step": e2e_s * 1e3 / e2e_steps},
         "roofline": {"bound": "hbm",
                      "kernel": f"fft_matvec (3 launches: slab forward, x pass, slab inverse; {mx}x{my}x{mz} FFT)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

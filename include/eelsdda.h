@@ -155,9 +155,12 @@ int eels_padded_dims(const eels_ctx* ctx, int* mx, int* my, int* mz);
 
 /* Tile widths (z-adjacent lines per block, 8, 16 or 32) of the FFT x pass
  * in FP32 and FP64 that the library picked for the current grid by timing
- * each width on the first eels_solve after eels_set_grid (no counterpart in
+ * each width on the first eels_solve of a lattice shape (no counterpart in
  * the paper: a tuning step of this implementation).  0 until that solve has
- * run (a size heuristic is used meanwhile). */
+ * run (a size heuristic is used meanwhile).  The choices of every timed
+ * shape (lattice and padded dims, contiguous columns, number of materials)
+ * are kept by the context: eels_set_grid of a shape timed before restores
+ * them instead of timing again. */
 int eels_tile_widths(const eels_ctx* ctx, int* xw32, int* xw64);
 
 /* Choices the library timed for the register x pass of the current grid
@@ -168,6 +171,15 @@ int eels_tile_widths(const eels_ctx* ctx, int* xw32, int* xw64);
  * one energy one block takes (its staged D-hat serves all of them).  0 and
  * 0 until that solve has run, or when the grid does not use that pass. */
 int eels_tuned_xpass(const eels_ctx* ctx, int* mode, int* spb);
+
+/* Every candidate the library timed for the register x pass of the current
+ * grid shape (see eels_tuned_xpass): *n receives their number, and the first
+ * min(cap, *n) go to mode[i], spb[i] and ms[i] (milliseconds of three
+ * launches on the batch of the first solve).  *n = 0 before that solve or when
+ * the grid does not use that pass.  Host arrays of cap entries (cap = 0 only
+ * counts).  EELS_E_INVALID_ARG for a NULL n or arrays, EELS_E_NO_GRID without
+ * a grid. */
+int eels_xpass_timings(const eels_ctx* ctx, int cap, int* n, int* mode, int* spb, float* ms);
 
 /*
  * Solve every (energy, beam) point and reduce the losses.  Host buffers.

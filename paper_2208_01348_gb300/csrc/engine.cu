@@ -259,6 +259,14 @@ struct eels_ctx {
     // the x pass reuses a staged D-hat tile over up to this many of them;
     // spb_tuned is the autotuner's choice for the lattice (0: not tuned yet)
     int spb = 1, spb_tuned = 0;
+    // the autotuner's choices per lattice shape (dims, padded dims, column
+    // structure, materials), kept across eels_set_grid calls
+    struct Tuned { int xw32, xw64, xmode, spb; std::vector<std::array<float, 3>> log; };
+    std::vector<std::array<float, 3>> xreg_log;   // the register x pass's timed candidates
+    std::map<std::array<int, 8>, Tuned> tune_cache;
+    std::array<int, 8> shape_key() const {
+        return {L.Nx, L.Ny, L.Nz, L.Mx, L.My, L.Mz, L.contig, L.nmat};
+    }
 
     std::vector<DevBuf*> buffers() {
         std::vector<DevBuf*> v = {&cellmap, &mat, &dip_cell, &col_range, &colinfo, &e64, &b64, &x64, &r64, &y64, &U, &u64, &u32,
@@ -395,6 +403,17 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     c->L.xw32 = c->L.xw64 = 0;
     c->L.xmode = 0;
     c->spb_tuned = 0;
+    const auto t = c->tune_cache.find(c->shape_key());
+    if (t != c->tune_cache.end()) {
+        c->L.xw32 = t->second.xw32;
+        c->L.xw64 = t->second.xw64;
+        c->L.xmode = t->second.xmode;
+        c->spb_tuned = t->second.spb;
+        c->xreg_log = t->second.log;
+        c->tuned = true;
+    } else {
+        c->xreg_log.clear();
+    }
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
 }
 
@@ -658,11 +677,39 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
     const void* ek;
     std::memcpy(&ek, &epsv, sizeof(ek));
     key.push_back(ek);
+    const int max_chunks = inner_cap(o, sizeof(Rl) == 4) / CHUNK + 2;
+    int* chunks = c->counters.as<int>() + 2;
     if (!c->graph || c->graph_key != key) {
         if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        // The whole inner solve is one graph: a WHILE node whose body runs
+        // CHUNK iterations and then the loop-control kernel, which ends the
+        // loop once no system is active or max_chunks chunks have run.
         cudaGraph_t g;
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        CK(cudaGraphCreate(&g, 0));
+        struct GraphGuard { cudaGraph_t g; ~GraphGuard() { cudaGraphDestroy(g); } } gguard{g};
+        cudaGraphConditionalHandle cond;
+        CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        CK(cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &np));
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         g_capturing = true;
+        // a launch that fails inside the capture throws: end the capture on the way out
+        struct CaptureGuard {
+            cudaStream_t st;
+            ~CaptureGuard() {
+                if (!g_capturing) return;
+                g_capturing = false;
+                cudaGraph_t partial = nullptr;
+                cudaStreamEndCapture(st, &partial);
+                cudaGetLastError();
+            }
+        } cguard{st};
         for (int n = 1; n <= CHUNK; ++n) {
             if (bicg) {
                 launch_matvec<Rl>(c->L, mv_args<Rl>(c, S, k.Pb, k.Vb, dr_of<Rl>(c), k.active, true), st);
@@ -683,40 +730,35 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
             launch_matvec<Rl>(c->L, a, st);
             launch_qmr_post_matvec<Rl>(k, n, fused, st);
         }
+        launch_loop_ctl(cond, k.n_active, chunks, max_chunks, st);
         g_capturing = false;
-        CK(cudaStreamEndCapture(st, &g));
+        cudaGraph_t captured;
+        CK(cudaStreamEndCapture(st, &captured));
         CK(cudaGraphInstantiate(&c->graph, g, 0));
+        // kernels per pass of the body (one chunk)
         size_t nn = 0;
-        cudaGraphGetNodes(g, nullptr, &nn);
+        cudaGraphGetNodes(body, nullptr, &nn);
         std::vector<cudaGraphNode_t> nodes(nn);
-        cudaGraphGetNodes(g, nodes.data(), &nn);
+        cudaGraphGetNodes(body, nodes.data(), &nn);
         c->graph_kernels = 0;
         for (auto& nd : nodes) {
             cudaGraphNodeType ty;
             cudaGraphNodeGetType(nd, &ty);
             if (ty == cudaGraphNodeTypeKernel) ++c->graph_kernels;
         }
-        cudaGraphDestroy(g);
         c->graph_key = key;
     }
-    int it = 0;
-    // The host reads the number of active systems between bursts of graph
-    // replays; a burst grows from 1 to 8 replays as the solve goes on (a
-    // replay after every system has converged only launches empty blocks).
-    const int max_chunks = inner_cap(o, sizeof(Rl) == 4) / CHUNK + 2;
-    int burst = 1;
-    for (int ch = 0; ch < max_chunks;) {
-        CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (*c->pinned <= 0) break;
-        for (int b = 0; b < burst && ch < max_chunks; ++b, ++ch) {
-            CK(cudaGraphLaunch(c->graph, st));
-            g_kernel_launches += c->graph_kernels;
-            it += CHUNK;
-        }
-        burst = std::min(8, burst * 2);
-    }
-    return it;
+    // One launch per inner solve; the host waits once, for the chunk count.
+    CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (*c->pinned <= 0) return 0;
+    CK(cudaMemsetAsync(chunks, 0, sizeof(int), st));
+    CK(cudaGraphLaunch(c->graph, st));
+    CK(cudaMemcpyAsync(c->pinned, chunks, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int n_chunks = *c->pinned;
+    g_kernel_launches += (long long)n_chunks * c->graph_kernels;
+    return n_chunks * CHUNK;
 }
 
 // Up to max_rounds refinement rounds with inner solves in precision Rl, on
@@ -1044,7 +1086,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
                 int mode = 0, spb = 1;
                 autotune_xreg(L, mv_args<float>(c, S, c->u32.as<float2>(), c->kv[5].as<float2>(), c->Dr32.as<float2>(),
                                                  nullptr, true),
-                              c->spb, st, &mode, &spb);
+                              c->spb, st, &mode, &spb, &c->xreg_log);
                 c->L.xmode = mode;
                 c->spb_tuned = spb;
                 c->spb = std::min(c->spb, spb);
@@ -1058,6 +1100,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
                                                                    c->y64.as<double2>(), c->Dr64.as<double2>(),
                                                                    nullptr, true), st);
             c->tuned = true;
+            c->tune_cache[c->shape_key()] = {c->L.xw32, c->L.xw64, c->L.xmode, c->spb_tuned, c->xreg_log};
         }
         refine_batch(c, S, o, fp64, it_b, rf_b, rs_b);
         // losses
@@ -1265,6 +1308,18 @@ int eels_tuned_xpass(const eels_ctx* c, int* mode, int* spb) {
     if (!c->has_grid) return EELS_E_NO_GRID;
     *mode = c->L.xmode;
     *spb = c->spb_tuned;
+    return EELS_OK;
+}
+
+int eels_xpass_timings(const eels_ctx* c, int cap, int* n, int* mode, int* spb, float* ms) {
+    if (!c || !n || cap < 0 || (cap > 0 && (!mode || !spb || !ms))) return EELS_E_INVALID_ARG;
+    if (!c->has_grid) return EELS_E_NO_GRID;
+    *n = (int)c->xreg_log.size();
+    for (int i = 0; i < cap && i < *n; ++i) {
+        mode[i] = (int)c->xreg_log[i][0];
+        spb[i] = (int)c->xreg_log[i][1];
+        ms[i] = c->xreg_log[i][2];
+    }
     return EELS_OK;
 }
 

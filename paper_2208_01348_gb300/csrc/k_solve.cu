@@ -551,6 +551,18 @@ template void launch_qmr2_init<double>(const KrylovArgs<double>&, cudaStream_t);
 template void launch_qmr2_post_matvec<float>(const KrylovArgs<float>&, bool, cudaStream_t);
 template void launch_qmr2_post_matvec<double>(const KrylovArgs<double>&, bool, cudaStream_t);
 
+// One thread: the chunk count bounds the loop whatever the systems do.
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, const int* n_active, int* chunks, int max_chunks) {
+    const int n = *chunks + 1;
+    *chunks = n;
+    cudaGraphSetConditional(h, (*n_active > 0 && n < max_chunks) ? 1u : 0u);
+}
+
+void launch_loop_ctl(cudaGraphConditionalHandle h, const int* n_active, int* chunks, int max_chunks, cudaStream_t st) {
+    count_launch();
+    k_loop_ctl<<<1, 1, 0, st>>>(h, n_active, chunks, max_chunks);
+}
+
 // ------------------------------------------------------------- BiCGStab
 // van der Vorst (SIAM J. Sci. Stat. Comput. 13 (1992) 631) for a general
 // complex matrix: shadow residual r^ = r0 and the conjugated inner product

@@ -619,9 +619,11 @@ bool launch_xpass_reg(const LatticeDev& L, const MatvecArgs<float>& a, cudaStrea
     return true;
 }
 
-void autotune_xreg(const LatticeDev& L, const MatvecArgs<float>& a, int max_spb, cudaStream_t st, int* mode, int* spb) {
+void autotune_xreg(const LatticeDev& L, const MatvecArgs<float>& a, int max_spb, cudaStream_t st, int* mode, int* spb,
+                   std::vector<std::array<float, 3>>* log) {
     *mode = 0;
     *spb = 1;
+    if (log) log->clear();
     if (!a.Dx || !xpass_reg_supported(L)) return;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return;
@@ -649,6 +651,7 @@ void autotune_xreg(const LatticeDev& L, const MatvecArgs<float>& a, int max_spb,
                 cudaGetLastError();
                 continue;
             }
+            if (log) log->push_back({(float)m, (float)b, ms});
             if (best < 0.f || ms < best) { best = ms; *mode = m; *spb = b; }
         }
     }

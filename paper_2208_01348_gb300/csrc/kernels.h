@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <array>
 #include <vector>
 
 #include "common.cuh"
@@ -89,8 +90,10 @@ bool launch_xpass_reg(const LatticeDev& L, const MatvecArgs<float>& a, cudaStrea
 // during a stream capture) for each way of moving U (direct loads, tensor
 // copies when available) and each number of systems per block in
 // {1, 2, 4, 8, 16} up to max_spb, and returns the fastest in *mode, *spb.
-// The x pass transforms a.U in place: its contents are lost.
-void autotune_xreg(const LatticeDev& L, const MatvecArgs<float>& a, int max_spb, cudaStream_t st, int* mode, int* spb);
+// The x pass transforms a.U in place: its contents are lost.  *log
+// receives every timed candidate as (mode, spb, ms of three launches).
+void autotune_xreg(const LatticeDev& L, const MatvecArgs<float>& a, int max_spb, cudaStream_t st, int* mode, int* spb,
+                   std::vector<std::array<float, 3>>* log);
 
 // Bounded device-side waits that gave up since the library was loaded (each
 // one left its kernel's results incomplete).  Reading it synchronises the device.

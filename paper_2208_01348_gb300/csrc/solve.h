@@ -88,6 +88,11 @@ template <typename Rl> void launch_bicg_init(const KrylovArgs<Rl>& k, cudaStream
 template <typename Rl> void launch_bicg_stage1(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Vb = A Pb
 template <typename Rl> void launch_bicg_stage2(const KrylovArgs<Rl>& k, cudaStream_t st);   // after Tb = A S
 
+// Loop control of a captured inner solve (the last node of the body of a
+// graph WHILE node): counts the chunk in *chunks and keeps the loop going
+// while any system is active and fewer than max_chunks chunks have run.
+void launch_loop_ctl(cudaGraphConditionalHandle h, const int* n_active, int* chunks, int max_chunks, cudaStream_t st);
+
 // ---- FP64 refinement helpers (vectors [S][n3]) ----
 // b = coef[mat] * e; x = 0; r = b
 void launch_rhs_init(const LatticeDev& L, int S, const double2* e, const double2* coef, double2* b, double2* x,

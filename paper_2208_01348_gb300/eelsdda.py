@@ -116,6 +116,8 @@ _sig = {
     "eels_vacuum_equivalent": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(eels_vacuum_map)]),
     "eels_tile_widths": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "eels_tuned_xpass": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "eels_xpass_timings": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_float)]),
     "eels_matvec_dev_noalloc": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, _P]),
     "eels_krylov_solve_dev": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int, C.c_double, C.c_int,
                                         C.POINTER(C.c_int), C.POINTER(C.c_int), _P]),
@@ -460,6 +462,18 @@ def eels_tuned_xpass(ctx):
     a, b = C.c_int(), C.c_int()
     _check(_lib.eels_tuned_xpass(ctx, C.byref(a), C.byref(b)), ctx)
     return a.value, b.value
+
+
+def eels_xpass_timings(ctx):
+    """[(mode, beams per block, ms)] of every register x-pass candidate timed for the grid shape."""
+    n = C.c_int()
+    _check(_lib.eels_xpass_timings(ctx, 0, C.byref(n), None, None, None), ctx)
+    k = n.value
+    if k == 0:
+        return []
+    m, b, t = (C.c_int * k)(), (C.c_int * k)(), (C.c_float * k)()
+    _check(_lib.eels_xpass_timings(ctx, k, C.byref(n), m, b, t), ctx)
+    return [(m[i], b[i], float(t[i])) for i in range(min(k, n.value))]
 
 
 def eels_kernel_launches() -> int:

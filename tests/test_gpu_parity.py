@@ -373,15 +373,25 @@ def test_mixed_fp32_rounds_match_oracle_above_fp64_threshold(dd, ctx, solver):
 
 
 @pytest.mark.parametrize("dims", [(13, 9, 11), (20, 9, 16), (40, 6, 8)])
-def test_tile_autotuning_keeps_matvec_bits(dd, ctx, dims):
+def test_tile_autotuning_keeps_matvec_bits(dd, dims):
     """The first solve on a grid times the x-pass tile widths (and, for x
     lengths 64 and 128, how U moves and how many systems a block takes);
     matvecs before and after the choice are bit-identical (the choices only
-    regroup the same arithmetic)."""
+    regroup the same arithmetic), and setting a grid of the same shape again
+    restores the choices and their timings instead of timing again."""
+    ctx = dd.eels_create(0)
+    try:
+        _autotuning_case(dd, ctx, dims)
+    finally:
+        dd.eels_destroy(ctx)
+
+
+def _autotuning_case(dd, ctx, dims):
     occ = _random_grid(dims, seed=21, nmat=2)
     dd.eels_set_grid(ctx, occ, 1.7)
     assert dd.eels_tile_widths(ctx) == (0, 0)
     assert dd.eels_tuned_xpass(ctx) == (0, 0)
+    assert dd.eels_xpass_timings(ctx) == []
     eps_p, eps_h = [I.drude(2.2), 2.0 + 0.5j], 1.9 + 0j
     x = I.random_complex((2, dd.eels_num_dipoles(ctx), 3), seed=8)
     y_before = [dd.eels_apply_matrix(ctx, pr, 2.2, eps_p, eps_h, x) for pr in (dd.EELS_FP64, dd.EELS_MIXED)]
@@ -390,13 +400,21 @@ def test_tile_autotuning_keeps_matvec_bits(dd, ctx, dims):
     w32, w64 = dd.eels_tile_widths(ctx)
     assert w32 in (8, 16, 32) and w64 in (8, 16, 32)
     mode, spb = dd.eels_tuned_xpass(ctx)
+    timings = dd.eels_xpass_timings(ctx)
     if dd.eels_padded_dims(ctx)[0] in (64, 128):
         assert mode in (1, 2) and spb == 1
+        assert timings and all(t[2] > 0 for t in timings)
+        best = min(timings, key=lambda t: t[2])
+        assert (best[0], best[1]) == (mode, spb)
     else:
-        assert (mode, spb) == (0, 0)
+        assert (mode, spb) == (0, 0) and timings == []
     y_after = [dd.eels_apply_matrix(ctx, pr, 2.2, eps_p, eps_h, x) for pr in (dd.EELS_FP64, dd.EELS_MIXED)]
     for a, b in zip(y_before, y_after):
         assert np.array_equal(a, b)
+    dd.eels_set_grid(ctx, occ, 1.7)
+    assert dd.eels_tile_widths(ctx) == (w32, w64)
+    assert dd.eels_tuned_xpass(ctx) == (mode, spb)
+    assert dd.eels_xpass_timings(ctx) == timings
 
 
 # ------------------------------------------------------------------ electron direction
