@@ -349,7 +349,7 @@ def run_serve(args):
             if dt > 0:
                 time.sleep(dt)
             w = r.workload
-            o = dd.eels_default_opts(ekin_keV=w.ekin_keV, eps_it=1e-8, n_dir=w.n_dir)
+            o = dd.eels_default_opts(ekin_keV=w.ekin_keV, eps_it=1e-8, n_dir=w.n_dir, device_loop=int(args.device_loop))
             ids.append((dd.eels_server_submit(srv, w.grid.occ, w.grid.d_nm, o, w.energies_eV, w.eps_p, w.eps_h,
                                               w.beams_nm), w))
         lat, pts, t_first, t_last = [], 0, None, 0.0
@@ -392,7 +392,8 @@ def run_serve(args):
         "config": {"workload": (f"serving stream (seed 20261203, lattices 16^3-96^3 spheres/rods, Au/Ag, three hosts, "
                                 f"1-256 beams, 8-128 energies): first {args.serve_requests} requests, each cut to "
                                 f"{args.serve_energies} energies x its first {args.serve_beams} beams"),
-                   "concurrency": args.serve_concurrency},
+                   "concurrency": args.serve_concurrency,
+                   "inner_loop": "device" if args.device_loop else "host bursts"},
         "latency_ms": {"p50": main_pass["p50_ms"], "p99": main_pass["p99_ms"], "max": main_pass["max_ms"]},
         "passes": {f"{int(r)}/s": v for r, v in passes.items()},
         "e2e": {"value": main_pass["points_per_s"], "unit": "points/s", "h2d_bytes_per_step": 0,
@@ -422,6 +423,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--solver", default="qmr2", choices=["qmr2", "qmr", "bicgstab"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--device-loop", action="store_true",
+                    help="each inner solve as one graph launch with a WHILE node (eels_opts.device_loop)")
     ap.add_argument("--fp64-sample", type=int, default=5,
                     help="energies of the plain FP64 single-system comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=0,
@@ -471,7 +474,8 @@ def main():
     g = w.grid
     prec = dd.EELS_MIXED if args.precision == "mixed" else dd.EELS_FP64
     opts = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=prec, eps_it=1e-8, eps_inner=1e-5, n_dir=w.n_dir,
-                                solver={"qmr2": dd.EELS_QMR2, "qmr": dd.EELS_QMR, "bicgstab": dd.EELS_BICGSTAB}[args.solver])
+                                solver={"qmr2": dd.EELS_QMR2, "qmr": dd.EELS_QMR, "bicgstab": dd.EELS_BICGSTAB}[args.solver],
+                                device_loop=int(args.device_loop))
     dd.eels_set_grid(ctx, g.occ, g.d_nm)
 
     # one step = one batch of the workload: E consecutive energies (all beams);
@@ -603,7 +607,7 @@ def main():
         "data": "synthetic (Drude permittivities stand in for tabulated optical data)",
         "config": {"workload": w.name, "points_per_gpu": n_e * n_beam, "points_per_step": E * n_beam,
                    "step": f"{E} energies x {n_beam} beams, batches cycled", "dipoles": n, "fft": [mx, my, mz],
-                   "precision": args.precision, "solver": args.solver, "x_tile": list(tiles),
+                   "precision": args.precision, "solver": args.solver, "inner_loop": "device" if args.device_loop else "host bursts", "x_tile": list(tiles),
                    "x_pass": {"mode": xnames[xtuned[0]], "beams_per_block": xtuned[1], "timed_ms": xtimed},
                    "eps_it": 1e-8,
                    "eps_inner": 1e-5, "n_dir": w.n_dir,

@@ -114,6 +114,13 @@ typedef struct {
                                 the direction option of its solver, Sec. S5) */
     int interaction;         /* EELS_INT_POINT (default) or EELS_INT_IGT_SO */
     int polarizability;      /* EELS_POL_CM (default) or EELS_POL_IGT_SO */
+    int device_loop;         /* 0 (default): the host launches the captured iterations in bursts of
+                                1 to 8 graph replays and reads the number of active systems between
+                                bursts; 1: each inner solve is one graph launch whose WHILE node
+                                repeats the captured iterations until no system is active or the
+                                iteration budget is spent (no host wait inside a solve; profilers
+                                that cannot see into conditional graphs then see none of its kernels).
+                                Results are bit-identical either way */
 } eels_opts;
 
 typedef struct {

@@ -677,26 +677,32 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
     const void* ek;
     std::memcpy(&ek, &epsv, sizeof(ek));
     key.push_back(ek);
+    const bool dev_loop = o->device_loop != 0;
+    key.push_back((const void*)(size_t)dev_loop);
     const int max_chunks = inner_cap(o, sizeof(Rl) == 4) / CHUNK + 2;
     int* chunks = c->counters.as<int>() + 2;
     if (!c->graph || c->graph_key != key) {
         if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-        // The whole inner solve is one graph: a WHILE node whose body runs
-        // CHUNK iterations and then the loop-control kernel, which ends the
-        // loop once no system is active or max_chunks chunks have run.
+        // The graph holds CHUNK captured iterations.  With the device loop it
+        // is a WHILE node whose body runs them and then the loop-control
+        // kernel, which ends the loop once no system is active or max_chunks
+        // chunks have run; without, the captured iterations are the graph.
         cudaGraph_t g;
         CK(cudaGraphCreate(&g, 0));
         struct GraphGuard { cudaGraph_t g; ~GraphGuard() { cudaGraphDestroy(g); } } gguard{g};
-        cudaGraphConditionalHandle cond;
-        CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
-        cudaGraphNodeParams np{};
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = cond;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        cudaGraphNode_t cnode;
-        CK(cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &np));
-        cudaGraph_t body = np.conditional.phGraph_out[0];
+        cudaGraph_t body = g;
+        cudaGraphConditionalHandle cond{};
+        if (dev_loop) {
+            CK(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np{};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = cond;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t cnode;
+            CK(cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &np));
+            body = np.conditional.phGraph_out[0];
+        }
         CK(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
         g_capturing = true;
         // a launch that fails inside the capture throws: end the capture on the way out
@@ -730,7 +736,7 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
             launch_matvec<Rl>(c->L, a, st);
             launch_qmr_post_matvec<Rl>(k, n, fused, st);
         }
-        launch_loop_ctl(cond, k.n_active, chunks, max_chunks, st);
+        if (dev_loop) launch_loop_ctl(cond, k.n_active, chunks, max_chunks, st);
         g_capturing = false;
         cudaGraph_t captured;
         CK(cudaStreamEndCapture(st, &captured));
@@ -748,17 +754,35 @@ int inner_solve(eels_ctx* c, int S, const eels_opts* o, double eps) {
         }
         c->graph_key = key;
     }
-    // One launch per inner solve; the host waits once, for the chunk count.
     CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (*c->pinned <= 0) return 0;
-    CK(cudaMemsetAsync(chunks, 0, sizeof(int), st));
-    CK(cudaGraphLaunch(c->graph, st));
-    CK(cudaMemcpyAsync(c->pinned, chunks, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const int n_chunks = *c->pinned;
-    g_kernel_launches += (long long)n_chunks * c->graph_kernels;
-    return n_chunks * CHUNK;
+    if (dev_loop) {
+        // one launch per inner solve; the host waits once, for the chunk count
+        CK(cudaMemsetAsync(chunks, 0, sizeof(int), st));
+        CK(cudaGraphLaunch(c->graph, st));
+        CK(cudaMemcpyAsync(c->pinned, chunks, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int n_chunks = *c->pinned;
+        g_kernel_launches += (long long)n_chunks * c->graph_kernels;
+        return n_chunks * CHUNK;
+    }
+    // The host reads the number of active systems between bursts of graph
+    // replays; a burst grows from 1 to 8 replays as the solve goes on (a
+    // replay after every system has converged only launches empty blocks).
+    int it = 0, burst = 1;
+    for (int ch = 0; ch < max_chunks;) {
+        for (int b = 0; b < burst && ch < max_chunks; ++b, ++ch) {
+            CK(cudaGraphLaunch(c->graph, st));
+            g_kernel_launches += c->graph_kernels;
+            it += CHUNK;
+        }
+        burst = std::min(8, burst * 2);
+        CK(cudaMemcpyAsync(c->pinned, k.n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*c->pinned <= 0) break;
+    }
+    return it;
 }
 
 // Up to max_rounds refinement rounds with inner solves in precision Rl, on
@@ -1221,6 +1245,7 @@ void eels_default_opts(eels_opts* o) {
     o->beam_dir[2] = 1.0;
     o->interaction = EELS_INT_POINT;
     o->polarizability = EELS_POL_CM;
+    o->device_loop = 0;
 }
 
 int eels_set_interaction(eels_ctx* c, int interaction, int polarizability) {

@@ -58,7 +58,8 @@ class eels_opts(C.Structure):
     _fields_ = [("ekin_keV", C.c_double), ("precision", C.c_int), ("solver", C.c_int),
                 ("eps_it", C.c_double), ("eps_inner", C.c_double), ("max_iter", C.c_int),
                 ("n_dir", C.c_int), ("max_batch", C.c_int), ("inner_max_iter", C.c_int),
-                ("beam_dir", C.c_double * 3), ("interaction", C.c_int), ("polarizability", C.c_int)]
+                ("beam_dir", C.c_double * 3), ("interaction", C.c_int), ("polarizability", C.c_int),
+                ("device_loop", C.c_int)]
 
 
 class eels_point_stats(C.Structure):
