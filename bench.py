@@ -62,8 +62,8 @@ CPU_SAMPLE = {"spectrum": (100, 0, None), "small": (0, 0, None),
 # measured on the workload TRAFFIC_WORKLOAD with kernel sources that hash to
 # TRAFFIC_SRC_HASH; reported as null for other workloads (other FFT sizes,
 # other kernels) and when the kernel sources differ from the measured ones.
-TRAFFIC_BYTES_PER_SYSTEM = 115_781_008   # 1,852,496,128 B over 16 systems, 128^3 FFT
-TRAFFIC_SRC_HASH = "363b1e37f9ac0e7b"
+TRAFFIC_BYTES_PER_SYSTEM = 115_766_848   # 1,852,269,568 B over 16 systems, 128^3 FFT
+TRAFFIC_SRC_HASH = "1ee292d212c5f1ea"
 TRAFFIC_WORKLOAD = "cherenkov"
 
 
@@ -423,6 +423,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--solver", default="qmr2", choices=["qmr2", "qmr", "bicgstab"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner-max-iter", type=int, default=0,
+                    help="FP32 iterations per inner solve before the FP64 restart (0: the library default)")
     ap.add_argument("--device-loop", action="store_true",
                     help="each inner solve as one graph launch with a WHILE node (eels_opts.device_loop)")
     ap.add_argument("--fp64-sample", type=int, default=5,
@@ -476,6 +478,8 @@ def main():
     opts = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=prec, eps_it=1e-8, eps_inner=1e-5, n_dir=w.n_dir,
                                 solver={"qmr2": dd.EELS_QMR2, "qmr": dd.EELS_QMR, "bicgstab": dd.EELS_BICGSTAB}[args.solver],
                                 device_loop=int(args.device_loop))
+    if args.inner_max_iter > 0:
+        opts.inner_max_iter = args.inner_max_iter
     dd.eels_set_grid(ctx, g.occ, g.d_nm)
 
     # one step = one batch of the workload: E consecutive energies (all beams);
@@ -607,7 +611,8 @@ def main():
         "data": "synthetic (Drude permittivities stand in for tabulated optical data)",
         "config": {"workload": w.name, "points_per_gpu": n_e * n_beam, "points_per_step": E * n_beam,
                    "step": f"{E} energies x {n_beam} beams, batches cycled", "dipoles": n, "fft": [mx, my, mz],
-                   "precision": args.precision, "solver": args.solver, "inner_loop": "device" if args.device_loop else "host bursts", "x_tile": list(tiles),
+                   "precision": args.precision, "solver": args.solver, "inner_loop": "device" if args.device_loop else "host bursts",
+                   "inner_max_iter": opts.inner_max_iter, "x_tile": list(tiles),
                    "x_pass": {"mode": xnames[xtuned[0]], "beams_per_block": xtuned[1], "timed_ms": xtimed},
                    "eps_it": 1e-8,
                    "eps_inner": 1e-5, "n_dir": w.n_dir,

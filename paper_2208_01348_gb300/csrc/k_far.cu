@@ -8,7 +8,9 @@
 // so each thread evaluates one exponential per (direction, column) and walks
 // the column with a constant step factor exp(-i kappa n_z).  Column dipoles
 // are staged in shared memory and read by every thread (broadcast).
-// Column partial sums are added in FP64.
+// The columns of one staged round are summed in the working precision and
+// each round's sum is added in FP64 (this part's FP64 rate is a small
+// fraction of its FP32 rate: FP64 work per column would bound the kernel).
 #include "solve.h"
 
 namespace eels {
@@ -46,6 +48,7 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(LatticeDev L, const cx<Rl>*
     double w = 0;
     if (valid) { n[0] = dirs[3 * dn]; n[1] = dirs[3 * dn + 1]; n[2] = dirs[3 * dn + 2]; w = wts[dn]; }
     const C step = cvt<C>(expmi<double>(kap, n[2]));
+    const Rl nx = (Rl)n[0], ny = (Rl)n[1], nz = (Rl)n[2];
     double2 S[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
     const size_t N = (size_t)L.N;
     const C* us = u + (size_t)s * 3 * N;
@@ -63,14 +66,17 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(LatticeDev L, const cx<Rl>*
         }
         __syncthreads();
         if (!valid) continue;
+        C R0 = mk<C>(0.0, 0.0), R1 = R0, R2 = R0;     // this round's columns
         for (int cc = 0; cc < FAR_CC; ++cc) {
             const int colid = c0 + cc;
             if (colid >= ncol) break;
             const int2 rg = L.col_range[colid];
             if (rg.x >= rg.y) continue;
             const int ix = colid % L.Nx, iy = colid / L.Nx;
-            const double xr = (ix + 0.5) - 0.5 * L.Nx, yr = (iy + 0.5) - 0.5 * L.Ny, zr = (rg.x + 0.5) - 0.5 * Nz;
-            C e = expmi<Rl>(kap, (Rl)(n[0] * xr + n[1] * yr + n[2] * zr));
+            // cell centres relative to the lattice centre (exact in either precision)
+            const Rl xr = (Rl)(2 * ix + 1 - L.Nx) * (Rl)0.5, yr = (Rl)(2 * iy + 1 - L.Ny) * (Rl)0.5,
+                     zr = (Rl)(2 * rg.x + 1 - Nz) * (Rl)0.5;
+            C e = expmi<Rl>(kap, nx * xr + ny * yr + nz * zr);
             C T0 = mk<C>(0.0, 0.0), T1 = T0, T2 = T0;
             const C* cx0 = col + (cc * 3) * Nz;
             for (int iz = rg.x; iz < rg.y; ++iz) {
@@ -79,10 +85,13 @@ __global__ void __launch_bounds__(FAR_THREADS) k_far(LatticeDev L, const cx<Rl>*
                 T2 = T2 + e * cx0[2 * Nz + iz];
                 e = e * step;
             }
-            S[0] = S[0] + widen(T0);
-            S[1] = S[1] + widen(T1);
-            S[2] = S[2] + widen(T2);
+            R0 = R0 + T0;
+            R1 = R1 + T1;
+            R2 = R2 + T2;
         }
+        S[0] = S[0] + widen(R0);
+        S[1] = S[1] + widen(R1);
+        S[2] = S[2] + widen(R2);
     }
     double val = 0.0;
     if (valid) {

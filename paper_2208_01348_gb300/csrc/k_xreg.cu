@@ -300,11 +300,13 @@ __global__ void __launch_bounds__(XR_THREADS, 4) k_xpass_reg(LatticeDev L, Matve
 template <int MX> struct XTma {
     static constexpr int ZT = XReg<MX>::ZT;
     static constexpr int TILE = 3 * (MX / 2) * ZT;      // float2 of a U tile (Nx <= MX/2)
-    // Mx = 128: rows of ZT = 8 elements (64 bytes) land with the 64-byte
-    // swizzle (the 16-byte chunk index within each row XORed with bits 1-2 of
-    // the row index), so that the rows p + 8r and columns of a warp's access
-    // fall on distinct banks; Mx = 64 keeps the plain layout
-    static constexpr bool SWZ = MX == 128;
+    // The tensor copies swizzle the tile's rows so that the rows p + 8r and
+    // columns of a warp's access fall on distinct banks: Mx = 128, rows of
+    // ZT = 8 elements (64 bytes), the 64-byte swizzle (the 16-byte chunk index
+    // within a row XORed with bits 1-2 of the row index); Mx = 64, rows of
+    // ZT = 16 elements (128 bytes), the 128-byte swizzle (XORed with bits 0-2)
+    static constexpr int ROW_SHIFT = MX == 128 ? 1 : 0;
+    static constexpr int CHUNKS = MX == 128 ? 4 : 8;     // 16-byte chunks per row
 };
 
 // Dynamic shared memory of k_xpass_tma (above the 48 KB of static arrays).
@@ -388,8 +390,8 @@ k_xpass_tma(LatticeDev L, MatvecArgs<float> a, const __grid_constant__ CUtensorM
     // element of (component c, row ix, this lane's column j) in a U tile
     auto uidx = [&](int c, int ix) -> int {
         const int r = c * Nx + ix;
-        if constexpr (XTma<MX>::SWZ) return r * ZT + ((((j >> 1) ^ ((r >> 1) & 3)) << 1) | (j & 1));
-        else return r * ZT + j;
+        constexpr int sh = XTma<MX>::ROW_SHIFT, mk = XTma<MX>::CHUNKS - 1;
+        return r * ZT + ((((j >> 1) ^ ((r >> sh) & mk)) << 1) | (j & 1));
     };
     int cur_slot = -1;
     unsigned ph_d = 0, ph_u[2] = {0, 0};
@@ -564,7 +566,8 @@ EncodeTiled encode_tiled() {
 }
 
 // U viewed as [3S][My][Nx][Mz] of 8-byte elements, box ZT x Nx x 1 x 3
-// (64-byte swizzle for 64-byte box rows, as XTma::SWZ expects).
+// (the 64-byte swizzle for 64-byte box rows, the 128-byte swizzle for
+// 128-byte rows, as the tile indexing of k_xpass_tma expects).
 bool u_tensor_map(const LatticeDev& L, const MatvecArgs<float>& a, int zt, CUtensorMap* map) {
     EncodeTiled enc = encode_tiled();
     if (!enc) return false;
@@ -574,7 +577,7 @@ bool u_tensor_map(const LatticeDev& L, const MatvecArgs<float>& a, int zt, CUten
     const cuuint32_t box[4] = {(cuuint32_t)zt, (cuuint32_t)L.Nx, 1, 3};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)a.U, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, zt == 8 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, zt == 8 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
