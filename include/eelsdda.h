@@ -131,11 +131,12 @@ typedef struct {
 } eels_point_stats;
 
 /* Fill opts with defaults: 100 keV, EELS_MIXED, EELS_QMR2, eps_it 1e-8,
- * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 1000,
+ * eps_inner 1e-5, max_iter 20000, n_dir 2562, max_batch 0, inner_max_iter 2000,
  * beam along +z, EELS_INT_POINT, EELS_POL_CM
  * (FP32 Lanczos recurrences lose biorthogonality on hard systems; restarting
- * every 1000 iterations from the FP64 residual keeps the iteration count
- * near that of the FP64 solve). */
+ * every 2000 iterations from the FP64 residual keeps the iteration count
+ * near that of the FP64 solve; 2000 was the fastest of 1000-4000 on the
+ * 128^3-FFT Cherenkov sphere and the rod map). */
 void eels_default_opts(eels_opts* opts);
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t

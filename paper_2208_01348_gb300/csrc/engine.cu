@@ -1239,7 +1239,7 @@ void eels_default_opts(eels_opts* o) {
     o->max_iter = 20000;
     o->n_dir = 2562;
     o->max_batch = 0;
-    o->inner_max_iter = 1000;
+    o->inner_max_iter = 2000;
     o->beam_dir[0] = 0.0;
     o->beam_dir[1] = 0.0;
     o->beam_dir[2] = 1.0;

@@ -1,5 +1,5 @@
 """Parity at the workloads' full sizes, in the launch configuration bench.py
-uses (mixed path, eps_it 1e-8, inner 1e-5 restarted every 1000 iterations).
+uses (mixed path, eps_it 1e-8, inner 1e-5 restarted every 2000 iterations).
 
 At these sizes a dense oracle solve is out of reach, so each sampled point is
 checked by the oracle in two independent ways:
