@@ -91,6 +91,13 @@ typedef struct {
     int nx, ny, nz;          /* lattice extents (cells) */
     double d_nm;             /* cell edge (dipole spacing) */
     const uint8_t* occ;      /* host, [nz][ny][nx], 0 = empty, k = material k (1-based) */
+    double origin_nm[3];     /* position of the lattice centre in the frame in which the beams
+                                (x0, y0) and the phase reference point z0 = 0 of Eq. 25 are given;
+                                0, 0, 0 = the lattice centred on the origin.  Moving the lattice
+                                by origin_nm is the same problem as moving every trajectory by
+                                -origin_nm (the probabilities change only through the beams'
+                                positions relative to the particle; p by the phase of the new
+                                reference point).  Must be finite (EELS_E_INVALID_ARG) */
 } eels_grid;
 
 typedef struct { double x0_nm, y0_nm; } eels_beam;   /* electron along +z, z0 = 0 */

@@ -231,6 +231,7 @@ struct eels_ctx {
     bool has_grid = false;
     int nx = 0, ny = 0, nz = 0, N = 0;
     double d_nm = 0;
+    double origin[3] = {0, 0, 0};  // lattice centre in the frame of the beams (lattice units)
     std::vector<int> cellmap_h;    // ABI layout cell -> ABI dipole index (x-fastest order), -1 empty
     std::vector<int> dip_cell_h;   // internal dipole -> cell index
     std::vector<int> abi_of;       // internal dipole -> ABI dipole index
@@ -308,6 +309,8 @@ void upload_twiddles(eels_ctx* c, int axis, int M) {
 void set_grid(eels_ctx* c, const eels_grid* g) {
     if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !(g->d_nm > 0) || !g->occ)
         throw Fail{EELS_E_INVALID_ARG, "grid: extents and d must be positive and occ non-NULL"};
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(g->origin_nm[a])) throw Fail{EELS_E_INVALID_ARG, "grid: origin must be finite"};
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const size_t ncell = (size_t)nx * ny * nz;
     // ABI numbering: occupied cells in x-fastest order (cellmap_h: cell -> ABI index)
@@ -372,6 +375,7 @@ void set_grid(eels_ctx* c, const eels_grid* g) {
     c->nx = nx; c->ny = ny; c->nz = nz;
     c->N = (int)c->dip_cell_h.size();
     c->d_nm = g->d_nm;
+    for (int a = 0; a < 3; ++a) c->origin[a] = g->origin_nm[a] / g->d_nm;
     c->max_mat = maxm;
     CK(cudaSetDevice(c->device));
     h2d(c->cellmap, cm_dev, c->stream);
@@ -506,18 +510,24 @@ BeamFrame beam_frame(const double* dir) {
     return f;
 }
 
-// Fills the electron fields of a SysField for beam b (lattice units).
-void set_beam(SysField& sf, const BeamFrame& f, const eels_beam& beam, double d_nm) {
-    const double x0 = beam.x0_nm / d_nm, y0 = beam.y0_nm / d_nm;
-    sf.x0 = x0;
-    sf.y0 = y0;
-    sf.px = x0 * f.e1[0] + y0 * f.e2[0];
-    sf.py = x0 * f.e1[1] + y0 * f.e2[1];
-    sf.pz = x0 * f.e1[2] + y0 * f.e2[2];
+// The z-electron kernels take the phase at z = 0 of the lattice frame: they
+// apply while the lattice centre has no z offset in the frame of the beams.
+bool z_path(const eels_ctx* c, const BeamFrame& f) { return f.along_z && c->origin[2] == 0.0; }
+
+// Fills the electron fields of a SysField for beam b in lattice units,
+// relative to the lattice centre: the trajectory through x0 e1 + y0 e2 of the
+// beams' frame, where the lattice centre sits at `origin`.
+void set_beam(SysField& sf, const BeamFrame& f, const eels_beam& beam, const eels_ctx* c) {
+    const double x0 = beam.x0_nm / c->d_nm, y0 = beam.y0_nm / c->d_nm;
+    sf.x0 = x0 - c->origin[0];
+    sf.y0 = y0 - c->origin[1];
+    sf.px = x0 * f.e1[0] + y0 * f.e2[0] - c->origin[0];
+    sf.py = x0 * f.e1[1] + y0 * f.e2[1] - c->origin[1];
+    sf.pz = x0 * f.e1[2] + y0 * f.e2[2] - c->origin[2];
     sf.nx = f.n[0];
     sf.ny = f.n[1];
     sf.nz = f.n[2];
-    sf.along_z = f.along_z ? 1 : 0;
+    sf.along_z = z_path(c, f) ? 1 : 0;
 }
 
 // An oblique electron must not cross an occupied cell: slab test of the line
@@ -525,7 +535,7 @@ void set_beam(SysField& sf, const BeamFrame& f, const eels_beam& beam, double d_
 void check_beams_dir(eels_ctx* c, int n_beam, const eels_beam* beams, const BeamFrame& f) {
     for (int b = 0; b < n_beam; ++b) {
         SysField sf{};
-        set_beam(sf, f, beams[b], c->d_nm);
+        set_beam(sf, f, beams[b], c);
         const double p[3] = {sf.px, sf.py, sf.pz}, n[3] = {f.n[0], f.n[1], f.n[2]};
         if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2]))
             throw Fail{EELS_E_INVALID_ARG, "beam position not finite"};
@@ -554,7 +564,8 @@ void check_beams_dir(eels_ctx* c, int n_beam, const eels_beam* beams, const Beam
 
 void check_beams(eels_ctx* c, int n_beam, const eels_beam* beams) {
     for (int b = 0; b < n_beam; ++b) {
-        const double x = beams[b].x0_nm / c->d_nm + 0.5 * c->nx, y = beams[b].y0_nm / c->d_nm + 0.5 * c->ny;
+        const double x = beams[b].x0_nm / c->d_nm - c->origin[0] + 0.5 * c->nx,
+                     y = beams[b].y0_nm / c->d_nm - c->origin[1] + 0.5 * c->ny;
         if (!std::isfinite(x) || !std::isfinite(y)) throw Fail{EELS_E_INVALID_ARG, "beam position not finite"};
         const int ix = (int)std::floor(x), iy = (int)std::floor(y);
         // the line crosses a cell (or touches its boundary) whose column holds a dipole
@@ -988,7 +999,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
     if (o->polarizability != EELS_POL_CM && o->polarizability != EELS_POL_IGT_SO)
         throw Fail{EELS_E_INVALID_ARG, "unknown polarizability"};
     const BeamFrame frame = beam_frame(o->beam_dir);
-    if (frame.along_z) check_beams(c, n_beam, beams);
+    if (z_path(c, frame)) check_beams(c, n_beam, beams);
     else check_beams_dir(c, n_beam, beams, frame);
     CK(cudaSetDevice(c->device));
     cudaStream_t st = c->stream;
@@ -1080,7 +1091,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
             sf[s].inv_gamma = d2(1.0 / p.gamma);
             sf[s].pref_unit = d2(p.pref_unit);
             sf[s].wdv = p.wdv;
-            set_beam(sf[s], frame, beams[b], c->d_nm);
+            set_beam(sf[s], frame, beams[b], c);
             for (int m = 0; m < EELS_MAX_MAT; ++m) {
                 coef[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? d2(p.sa[m]) : make_double2(0, 0);
                 wabs[(size_t)s * EELS_MAX_MAT + m] = m < n_mat ? p.wabs[m] : 0.0;
@@ -1091,7 +1102,7 @@ int solve_impl(eels_ctx* c, const eels_opts* o, int n_energy, const double* ener
         }
         h2d(c->sysf, sf, st); h2d(c->coef, coef, st); h2d(c->diag, diag, st); h2d(c->wabs, wabs, st);
         h2d(c->wdv, wdv, st); h2d(c->slot, slot, st); h2d(c->kappa_sys, kap, st);
-        launch_incident_field(L, S, c->sysf.as<SysField>(), frame.along_z, c->e64.as<double2>(), st);
+        launch_incident_field(L, S, c->sysf.as<SysField>(), z_path(c, frame), c->e64.as<double2>(), st);
         launch_rhs_init(L, S, c->e64.as<double2>(), c->coef.as<double2>(), c->b64.as<double2>(), c->x64.as<double2>(),
                         c->r64.as<double2>(), st);
         // y = A x for x = 0: refinement rounds recompute y only for the systems they update
@@ -1395,7 +1406,7 @@ int eels_incident_field_dir(eels_ctx* c, double ekin_keV, double energy_eV, eels
         if (!c->has_grid) throw Fail{EELS_E_NO_GRID, "eels_set_grid has not been called"};
         const double zdir[3] = {0.0, 0.0, 1.0};
         const BeamFrame frame = beam_frame(beam_dir ? beam_dir : zdir);
-        if (frame.along_z) check_beams(c, 1, &beam);
+        if (z_path(c, frame)) check_beams(c, 1, &beam);
         else check_beams_dir(c, 1, &beam, frame);
         CK(cudaSetDevice(c->device));
         const double d_m = c->d_nm * 1e-9;
@@ -1404,14 +1415,14 @@ int eels_incident_field_dir(eels_ctx* c, double ekin_keV, double energy_eV, eels
         SysField sf;
         sf.kt = d2(p.wdv / p.gamma); sf.inv_gamma = d2(1.0 / p.gamma); sf.pref_unit = d2(p.pref_unit);
         sf.wdv = p.wdv;
-        set_beam(sf, frame, beam, c->d_nm);
+        set_beam(sf, frame, beam, c);
         std::vector<SysField> sv(1, sf);
         cudaStream_t st = c->stream;
         h2d(c->sysf, sv, st);
         const size_t n3 = (size_t)3 * c->N;
         c->e64.ensure(n3 * sizeof(double2));
         c->y64.ensure(n3 * sizeof(double2));
-        launch_incident_field(c->L, 1, c->sysf.as<SysField>(), frame.along_z, c->e64.as<double2>(), st);
+        launch_incident_field(c->L, 1, c->sysf.as<SysField>(), z_path(c, frame), c->e64.as<double2>(), st);
         launch_aux_field(c->L, 1, c->sysf.as<SysField>(), c->e64.as<double2>(), c->y64.as<double2>(), st);
         std::vector<double2> h(n3), ha(n3);
         CK(cudaMemcpyAsync(h.data(), c->e64.p, n3 * sizeof(double2), cudaMemcpyDeviceToHost, st));

@@ -37,6 +37,7 @@ struct Job {
     // copies of the request
     int nx = 0, ny = 0, nz = 0;
     double d_nm = 0;
+    double origin_nm[3] = {0, 0, 0};
     std::vector<uint8_t> occ;
     eels_opts opts{};
     std::vector<double> energies;
@@ -102,7 +103,7 @@ void run_job(eels_server* s, Job* j, cudaStream_t st) {
     eels_ctx* ctx = nullptr;
     int rc = eels_create(&ctx, s->o.device, st);
     if (rc == EELS_OK) {
-        eels_grid g{j->nx, j->ny, j->nz, j->d_nm, j->occ.data()};
+        eels_grid g{j->nx, j->ny, j->nz, j->d_nm, j->occ.data(), {j->origin_nm[0], j->origin_nm[1], j->origin_nm[2]}};
         rc = eels_set_grid(ctx, &g);
         if (rc == EELS_OK)
             rc = eels_solve(ctx, &j->opts, ne, j->energies.data(), j->n_mat, j->eps_p.data(), j->eps_h.data(), nb,
@@ -211,6 +212,7 @@ int eels_server_submit(eels_server* s, const eels_grid* g, const eels_opts* o, i
         return EELS_E_INVALID_ARG;
     auto j = std::make_unique<Job>();
     j->nx = g->nx; j->ny = g->ny; j->nz = g->nz; j->d_nm = g->d_nm;
+    for (int a = 0; a < 3; ++a) j->origin_nm[a] = g->origin_nm[a];
     j->occ.assign(g->occ, g->occ + (size_t)g->nx * g->ny * g->nz);
     j->opts = *o;
     j->energies.assign(energy_eV, energy_eV + n_energy);

@@ -47,7 +47,7 @@ class eels_c128(C.Structure):
 
 class eels_grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("d_nm", C.c_double),
-                ("occ", C.POINTER(C.c_uint8))]
+                ("occ", C.POINTER(C.c_uint8)), ("origin_nm", C.c_double * 3)]
 
 
 class eels_beam(C.Structure):
@@ -191,15 +191,17 @@ def eels_last_error(ctx) -> str:
     return _lib.eels_last_error(ctx).decode()
 
 
-def _grid(occ: np.ndarray, d_nm: float):
+def _grid(occ: np.ndarray, d_nm: float, origin_nm=(0.0, 0.0, 0.0)):
     occ = np.ascontiguousarray(occ, dtype=np.uint8)
     nz, ny, nx = occ.shape
-    g = eels_grid(nx, ny, nz, float(d_nm), occ.ctypes.data_as(C.POINTER(C.c_uint8)))
+    g = eels_grid(nx, ny, nz, float(d_nm), occ.ctypes.data_as(C.POINTER(C.c_uint8)),
+                  (C.c_double * 3)(*[float(v) for v in origin_nm]))
     return g, occ
 
 
-def eels_set_grid(ctx, occ: np.ndarray, d_nm: float) -> None:
-    g, keep = _grid(occ, d_nm)
+def eels_set_grid(ctx, occ: np.ndarray, d_nm: float, origin_nm=(0.0, 0.0, 0.0)) -> None:
+    """occ [nz][ny][nx] material indices; origin_nm: lattice centre in the beams' frame."""
+    g, keep = _grid(occ, d_nm, origin_nm)
     _check(_lib.eels_set_grid(ctx, C.byref(g)), ctx)
 
 
@@ -520,8 +522,9 @@ def eels_server_create(device: int = 0, hbm_budget: int = 0, max_concurrent: int
     return h
 
 
-def eels_server_submit(srv, occ: np.ndarray, d_nm: float, opts: eels_opts, energies_eV, eps_p, eps_h, beams_nm) -> int:
-    g, keep = _grid(occ, d_nm)
+def eels_server_submit(srv, occ: np.ndarray, d_nm: float, opts: eels_opts, energies_eV, eps_p, eps_h, beams_nm,
+                       origin_nm=(0.0, 0.0, 0.0)) -> int:
+    g, keep = _grid(occ, d_nm, origin_nm)
     e = np.ascontiguousarray(energies_eV, dtype=np.float64).ravel()
     ep = _c128(eps_p).reshape(len(e), -1)
     eh = _c128(eps_h).ravel()

@@ -347,6 +347,38 @@ def test_async_solve_matches_blocking_solve(dd, ctx):
 
 
 
+@pytest.mark.parametrize("direction,origin,shift", [
+    ((0.0, 0.0, 1.0), (3.0, -2.0, 5.0), True),      # z electron: beams shift by (ox, oy), phase by oz
+    ((1.0, 1.0, 1.0), (4.0, 4.0, 4.0), False),      # origin along the direction: phase only
+])
+def test_grid_origin_translates_the_beams(dd, ctx, direction, origin, shift):
+    """A lattice centred at origin_nm is the centred lattice with every
+    trajectory moved by -origin_nm: the same probabilities, and dipole moments
+    times exp(i w s / v), s the move of the phase reference point along the
+    electron (FP64 path; LU-checked centred solves elsewhere pin the rest)."""
+    from oracle import physics
+    w = I.reduced(I.config_spectrum(), 10 / 32, n_energy=2)
+    o = dd.eels_default_opts(ekin_keV=w.ekin_keV, precision=dd.EELS_FP64, eps_it=1e-10, n_dir=162,
+                             beam_dir=direction)
+    beams = np.asarray(w.beams_nm, dtype=float)
+    org = np.asarray(origin)
+    dd.eels_set_grid(ctx, w.grid.occ, w.grid.d_nm, origin_nm=origin)
+    moved = dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, beams + (org[:2] if shift else 0.0),
+                          want_p=True)
+    dd.eels_set_grid(ctx, w.grid.occ, w.grid.d_nm)
+    ref = dd.eels_solve(ctx, o, w.energies_eV, w.eps_p, w.eps_h, beams, want_p=True)
+    for a, b in ((moved.p_eels, ref.p_eels), (moved.p_cl, ref.p_cl), (moved.p_ext, ref.p_ext),
+                 (moved.p_abs, ref.p_abs)):
+        assert np.allclose(a, b, rtol=1e-9, atol=0)
+    n = np.asarray(direction) / np.linalg.norm(direction)
+    s_m = float(org @ n) * 1e-9
+    v = physics.electron_speed(w.ekin_keV)
+    for e, E in enumerate(w.energies_eV):
+        ph = np.exp(1j * physics.omega_of(E) * s_m / v)
+        pm, pr = moved.p[e], ref.p[e]
+        assert np.linalg.norm(pm - ph * pr) <= 1e-8 * np.linalg.norm(pr)
+
+
 @pytest.mark.parametrize("solver", ["QMR2", "QMR", "BICGSTAB"])
 def test_device_loop_matches_host_loop(dd, ctx, solver):
     """Inner solves as one graph launch with a WHILE node (device_loop = 1)
