@@ -156,10 +156,12 @@ void eels_destroy(eels_ctx* ctx);
 /* Text of the context's last error ("" if none).  Valid until the next call. */
 const char* eels_last_error(const eels_ctx* ctx);
 
-/* Set the particle lattice (copies occ).  Returns EELS_E_INVALID_ARG for
- * non-positive extents or d, or an empty lattice; EELS_E_UNSUPPORTED if a
- * padded FFT length (smallest even 7-smooth >= 2n-1 per axis) exceeds 256
- * (more than 128 cells along an axis). */
+/* Set the particle lattice (copies occ and origin_nm).  Returns
+ * EELS_E_INVALID_ARG for non-positive extents or d, a non-finite origin, or
+ * an empty lattice; EELS_E_UNSUPPORTED if a padded FFT length (smallest even
+ * 7-smooth >= 2n-1 per axis) exceeds 256 (more than 128 cells along an axis).
+ * Tuning choices of a lattice shape timed before on this context are
+ * restored (eels_tile_widths). */
 int eels_set_grid(eels_ctx* ctx, const eels_grid* grid);
 
 /* Number of occupied cells of the current grid (dipoles N). */
@@ -179,8 +181,8 @@ int eels_padded_dims(const eels_ctx* ctx, int* mx, int* my, int* mz);
 int eels_tile_widths(const eels_ctx* ctx, int* xw32, int* xw64);
 
 /* Choices the library timed for the register x pass of the current grid
- * (FFT x lengths 64 and 128, FP32) on the first eels_solve after
- * eels_set_grid (no counterpart in the paper: a tuning step of this
+ * (FFT x lengths 64 and 128, FP32) on the first eels_solve of its shape
+ * (no counterpart in the paper: a tuning step of this
  * implementation): *mode 1 = U lines loaded and stored by the threads,
  * 2 = moved by tensor copies (TMA) through shared memory; *spb = beams of
  * one energy one block takes (its staged D-hat serves all of them).  0 and
